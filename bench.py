@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""Benchmark of the Jacobi3D hot path (3D 7-point Jacobi over a block-decomposed
+grid with per-iteration halo exchange through intra-device channels).
+
+One "step" is one pass of the whole hot path over the workload: `iters`
+Jacobi iterations of every block (stencil + fused face pack into the
+neighbours' receive slots + fused unpack) followed by the FP64 residual
+reduction and its read-back (the convergence test's input).  The default
+workload is the 512^3 FP64 grid in 8x8x8 blocks of 64^3, 1000 iterations per
+step; its two state copies (2.1 GB) exceed L2, so no flush is needed between
+steps.
+
+Output: ONE JSON line on rank 0 (see the keys below).  `--impl reference`
+times the CPU oracle instead (the slow, obviously-correct program the CUDA
+path is checked against), on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Jacobi GLUP/s and halo GB/s vs HBM roofline; served solves/sec, p50/p99 at 1e-6 resid"
+DEFAULT_WORKLOAD = "jacobi3d-fp64-512c-8x8x8"
+# Nominal FP64 pipe of the GB300: 1.25 TFLOP/s counting an FMA as two flops,
+# i.e. 0.625 T FP64 instructions/s; a DADD or DMUL is one flop per instruction.
+FP64_ADDMUL_PEAK_GFLOPS = 625.0
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    p.add_argument("--path", default="graph", choices=["fused", "graph", "persistent", "explicit"])
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--cpu-iters", type=int, default=4, help="oracle iterations in the CPU sample")
+    p.add_argument("--no-sweep", action="store_true", help="skip the channel ping-pong sweep")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return p.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for name in ("kernels.cu", "common.cuh", "kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_2102_12416_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu
+    summary, or None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", f"ncu_step_{workload}.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None, None
+    if d.get("source_sha") != kernel_source_sha():
+        return None, d
+    return d.get("dram_bytes_per_launch"), d
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 7:
+                continue
+            try:
+                sm.append(float(r[0]))
+                smax.append(float(r[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_config(w, name, path):
+    grid = list(w["grid"])
+    mode, v = w["split"]
+    if mode == "count":
+        blocks = list(v)
+        shape = [-(-g // b) for g, b in zip(grid, blocks)]
+    else:
+        shape = list(v)
+        blocks = [-(-g // b) for g, b in zip(grid, shape)]
+    return {"workload": name, "grid": grid, "blocks": blocks, "block_shape": shape, "dtype": w["dtype"],
+            "iters_per_step": w["iters"], "path": path,
+            "l2": "inputs larger than L2 (two state copies of %.2f GB each), no flush" %
+                  (grid[0] * grid[1] * grid[2] * (8 if w["dtype"] == "f64" else 4) / 1e9)}
+
+
+def cpu_baseline(w, iters):
+    import jacobi_inputs as J
+    import numpy as np
+    import oracle
+    oracle.build()
+    init = dict(bc=w["bc"], bc_seed=w["bc_seed"], interior=w["interior"], interior_seed=w["interior_seed"])
+    u0 = J.initial_grid(*w["grid"], dtype=np.float64 if w["dtype"] == "f64" else np.float32, **init)
+    t0 = time.perf_counter()
+    oracle.jacobi(u0, iters)
+    dt = time.perf_counter() - t0
+    n = w["grid"][0] * w["grid"][1] * w["grid"][2]
+    return {"value": n * iters / dt / 1e9, "unit": "GLUP/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{iters} of {w['iters']} iterations of the full {w['grid'][0]}x{w['grid'][1]}x{w['grid'][2]} "
+                      f"grid, monolithic C oracle, OpenMP over z-planes", "seconds": dt}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    import jacobi_inputs as J
+    w = J.WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        cpu_baseline(w, args.cpu_iters)
+    vals, secs = [], []
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline(w, args.cpu_iters)
+        vals.append(cb["value"])
+        secs.append(cb["seconds"])
+    value = len(vals) * (w["grid"][0] * w["grid"][1] * w["grid"][2] * args.cpu_iters) / sum(secs) / 1e9
+    cb = dict(cb, value=value)
+    cb.pop("seconds", None)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": w["dtype"], "data": "synthetic",
+            "config": workload_config(w, args.workload, "cpu-oracle"),
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def channel_sweep(jg, torch, s, stream):
+    """OSU-style ping-pong between two blocks' channel endpoints, 8 B .. 4 MB."""
+    ch = jg.channel_open(s.h, 1, 0, 1, 4 << 20)
+    out = []
+    try:
+        for k in range(20):
+            nbytes = 8 << k
+            ctas = max(1, min(64, nbytes // (128 << 10)))
+            rounds = 2000 if nbytes <= (64 << 10) else 200
+            jg.channel_pingpong(ch, nbytes, 50, ctas, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            jg.channel_pingpong(ch, nbytes, rounds, ctas, stream)
+            e1.record(stream)
+            e1.synchronize()
+            jg.channel_sync(ch, stream)
+            one_way_us = e0.elapsed_time(e1) * 1e3 / (2 * rounds)
+            out.append({"bytes": nbytes, "one_way_us": round(one_way_us, 3),
+                        "GBps": round(nbytes / (one_way_us * 1e-6) / 1e9, 3), "ctas_per_side": ctas})
+    finally:
+        jg.channel_close(ch)
+    return out
+
+
+def run_ours(args):
+    world, rank, local = dist_setup(args)
+    import torch
+    import jacobi_inputs as J
+    import paper_2102_12416_gb300 as jg
+    from paper_2102_12416_gb300 import _build
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(_build.LIB):
+        _build.build()
+    if dist:
+        dist.barrier()
+    jg.load()
+
+    w = J.WORKLOADS[args.workload]
+    iters = w["iters"]
+    init = dict(bc=w["bc"], bc_seed=w["bc_seed"], interior=w["interior"], interior_seed=w["interior_seed"])
+    if "noise_amp" in w:
+        init["noise_amp"] = w["noise_amp"]
+    stream = torch.cuda.Stream()
+    n_points = w["grid"][0] * w["grid"][1] * w["grid"][2]
+
+    # ---- device-resident timing ------------------------------------------------
+    s = jg.Jacobi3D(w["grid"], w["split"], w["dtype"], init, path=args.path, stream=stream)
+    info = s.info
+    for _ in range(args.warmup):
+        s.step(iters)
+        s.residual()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 2)]
+    ev[0].record(stream)
+    rel = None
+    for k in range(args.steps):
+        ev[2 + 2 * k].record(stream)
+        s.step(iters)
+        ev[3 + 2 * k].record(stream)
+        rel, _ = s.residual()
+    ev[1].record(stream)
+    ev[1].synchronize()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = ev[0].elapsed_time(ev[1])
+    stencil_ms = sum(ev[2 + 2 * k].elapsed_time(ev[3 + 2 * k]) for k in range(args.steps))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * n_points * iters * args.steps / (total_ms * 1e-3) / 1e9
+    launches = args.steps * (iters + 2)
+
+    # dominant kernel: the fused stencil step, one launch per iteration
+    launch_s = stencil_ms * 1e-3 / (args.steps * iters)
+    elem = 8 if w["dtype"] == "f64" else 4
+    peaks, peak_kind = measured_peaks()
+    traffic, _ = ncu_traffic(args.workload)
+    if w["dtype"] == "f64":
+        achieved = 6 * n_points / launch_s / 1e9
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_ADDMUL_PEAK_GFLOPS, "unit": "GFLOP/s",
+                    "frac": achieved / FP64_ADDMUL_PEAK_GFLOPS, "traffic": traffic,
+                    "kernel": "k_step<double, write|pack> (fused stencil + face pack)",
+                    "peak_kind": "nominal FP64 1.25 TFLOP/s (FMA=2) -> 0.625 T add/mul per s",
+                    "hbm_view": {"algorithmic_GBps": 2 * elem * n_points / launch_s / 1e9,
+                                 "peak": peaks["hbm_gbs"],
+                                 "frac": 2 * elem * n_points / launch_s / 1e9 / peaks["hbm_gbs"],
+                                 "peak_kind": peak_kind}}
+    else:
+        achieved = 2 * elem * n_points / launch_s / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                    "kernel": "k_step<float, write|pack> (fused stencil + face pack)", "peak_kind": peak_kind}
+    halo = {"payload_bytes_per_iter": info.halo_bytes_per_iter,
+            "GBps": info.halo_bytes_per_iter * iters * args.steps / (total_ms * 1e-3) / 1e9}
+
+    # ---- end to end through the C ABI with host buffers ------------------------
+    nx, ny, nz = w["grid"]
+    npdt = torch.float64 if w["dtype"] == "f64" else torch.float32
+    u0 = J.initial_grid(nx, ny, nz, dtype="float64" if w["dtype"] == "f64" else "float32", **init)
+    h_in = torch.from_numpy(u0).pin_memory()
+    h_out = torch.empty((nz, ny, nx), dtype=npdt).pin_memory()
+    s.set_state(u0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        jg.jacobi_set_state(s.h, 0, h_in.data_ptr(), False, stream)
+        s.step(iters)
+        s.residual()
+        jg.jacobi_copy_out(s.h, 0, h_out.data_ptr(), False, jg.JACOBI_LAYOUT_INTERIOR, stream)
+    e1.record(stream)
+    e1.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * n_points * iters * args.e2e_steps / (e2e_ms * 1e-3) / 1e9, "unit": "GLUP/s",
+           "h2d_bytes_per_step": h_in.numel() * h_in.element_size(),
+           "d2h_bytes_per_step": h_out.numel() * h_out.element_size() + 8 * 4, "steps": args.e2e_steps}
+
+    sweep = None
+    if not args.no_sweep and rank == 0:
+        sweep = channel_sweep(jg, torch, s, stream)
+    s.close()
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cb = cpu_baseline(w, args.cpu_iters)
+        cb.pop("seconds", None)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": w["dtype"], "data": "synthetic",
+                "config": dict(workload_config(w, args.workload, args.path),
+                               parallelism=f"replicas{world}" if world > 1 else "single-gpu"),
+                "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "halo": halo, "final_rel_residual": rel[0] if rel else None,
+                "channel_pingpong": sweep}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

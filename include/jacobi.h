@@ -1,0 +1,306 @@
+/*
+ * jacobi.h -- C ABI of the GB300 Jacobi3D library.
+ *
+ * The library runs the hot path of the proxy application in Sec. 4.3 of
+ * "Accelerating Communication for Parallel Programming Models on GPU Systems"
+ * (Choi et al., arXiv 2102.12416): the Jacobi iterative method on a 3D grid
+ * that is split into equal-size cuboid blocks (the paper's chares), each
+ * block exchanging halo faces with up to six neighbours every iteration.  On
+ * one GPU the exchange is a device-resident "channel" (Sec. 3.2.2, Channel
+ * API): the producer writes a face straight into the neighbour's
+ * preallocated receive slot and the consumer reads it there, with no
+ * host-side metadata message.
+ *
+ * Conventions for every call
+ *   - Returns JACOBI_OK (0) or a positive error code; jacobi_strerror() names
+ *     it and jacobi_last_error() returns a message for the calling thread.
+ *   - Handles are opaque, created and freed by the library.
+ *   - Device pointers passed in (workspace, channel buffers, copy targets) stay
+ *     owned by the caller and must outlive the handle that uses them.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is stream-ordered and asynchronous unless a call says it
+ *     synchronises.
+ *   - There is no host fallback: every numeric step runs in the library's
+ *     CUDA kernels (sm_103a).  Calls that need a GPU fail with JACOBI_ECUDA
+ *     when none is present.
+ *
+ * Data layout of a grid of nx*ny*nz interior points ("interior" layout): one
+ * array of nz*ny*nx values, x fastest.  The "padded" layout adds the
+ * Dirichlet boundary: (nz+2)*(ny+2)*(nx+2) values, x fastest, interior at
+ * indices 1..n on each axis.
+ *
+ * Arithmetic (the paper prints no stencil; this is the library's reading):
+ *   u'(i,j,k) = ((u(i-1)+u(i+1)) + (u(j-1)+u(j+1))) + (u(k-1)+u(k+1)),
+ *   then multiplied by 1/6 rounded to the state type; every operation is
+ *   rounded separately (no fused multiply-add), so an FP64 run is bit-exact
+ *   with a monolithic CPU evaluation in the same order, for any block split.
+ * Residual (an addition; the paper's Jacobi3D runs a fixed iteration count):
+ *   r = s - 6u in FP64 at every interior point, |r| = sqrt(sum r^2), b the same
+ *   expression with the interior set to zero, rel = |r| / |b|.
+ */
+#ifndef JACOBI_H
+#define JACOBI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+enum {
+  JACOBI_OK = 0,
+  JACOBI_EINVAL = 1,    /* bad argument (sizes, ids, null pointers, state) */
+  JACOBI_ENOMEM = 2,    /* device or host allocation failed, or workspace too small */
+  JACOBI_EBUSY = 3,     /* serving: no slot / HBM budget left right now */
+  JACOBI_EAGAIN = 4,    /* serving: result not ready yet */
+  JACOBI_ETIMEDOUT = 5, /* a device-side wait gave up (bounded spin expired) */
+  JACOBI_ECUDA = 6,     /* a CUDA runtime call failed (message in jacobi_last_error) */
+  JACOBI_ESEQ = 7       /* channel: sequence mismatch (message order broken) */
+};
+
+typedef enum { JACOBI_F64 = 0, JACOBI_F32 = 1 } jacobi_dtype;
+
+/* Dirichlet boundary families.  Coordinates are node-centred on the unit cube,
+ * x = i/(nx+1) (IEEE FP64 division), likewise y and z. */
+typedef enum {
+  JACOBI_BC_LINEAR = 0,       /* g = (x + 2y) + 3z                         */
+  JACOBI_BC_LINEAR_NOISE = 1, /* g + noise_amp * U(bc_seed, idx)           */
+  JACOBI_BC_UNIFORM = 2       /* U(bc_seed, idx)                           */
+} jacobi_bc;
+
+typedef enum {
+  JACOBI_INTERIOR_ZERO = 0,    /* interior starts at 0                    */
+  JACOBI_INTERIOR_UNIFORM = 1, /* U(interior_seed, idx)                   */
+  JACOBI_INTERIOR_BC = 2       /* the boundary function evaluated inside  */
+} jacobi_interior;
+
+/* Synthetic initial state.  U(seed, idx) is the idx-th output of SplitMix64
+ * seeded with `seed` (Steele, Lea, Flood, OOPSLA 2014), top 53 bits scaled by
+ * 2^-53; idx is the global padded linear index (k*(ny+2)+j)*(nx+2)+i, so the
+ * data does not depend on the block split.  FP32 states take the FP64 value
+ * rounded to nearest. */
+typedef struct {
+  int32_t bc;        /* jacobi_bc */
+  int32_t interior;  /* jacobi_interior */
+  uint64_t bc_seed;
+  uint64_t interior_seed;
+  double noise_amp;
+} jacobi_init;
+
+typedef struct { int64_t nx, ny, nz; } jacobi_dim3;
+
+/* Block split (Sec. 4.3: equal-size cuboid blocks).
+ *   JACOBI_SPLIT_COUNT: x,y,z = blocks per axis; extents differ by at most one
+ *                       point (the first n % p blocks get the extra point).
+ *   JACOBI_SPLIT_SHAPE: x,y,z = block extents; the last block on an axis is
+ *                       partial when the extent does not divide the grid. */
+typedef enum { JACOBI_SPLIT_COUNT = 0, JACOBI_SPLIT_SHAPE = 1 } jacobi_split_mode;
+typedef struct { int32_t mode; int32_t pad_; int64_t x, y, z; } jacobi_split;
+
+/* Step paths (all give bit-identical results).
+ *   FUSED:      one launch per iteration; each block's new boundary planes are
+ *               written straight into its neighbours' receive slots (pack and
+ *               channel transfer fused into the stencil epilogue) and read
+ *               from there by the next iteration (unpack fused into the load).
+ *   EXPLICIT:   stencil launch, then an explicit pack of every face into a
+ *               send buffer and a channel copy into the neighbour's slot.
+ *   PERSISTENT: one cooperative launch runs all iterations; blocks signal
+ *               neighbours with release/acquire progress flags in device
+ *               memory instead of kernel boundaries (bounded waits).
+ *   GRAPH:      the FUSED launches captured once in a CUDA graph and replayed. */
+typedef enum {
+  JACOBI_PATH_FUSED = 0,
+  JACOBI_PATH_EXPLICIT = 1,
+  JACOBI_PATH_PERSISTENT = 2,
+  JACOBI_PATH_GRAPH = 3
+} jacobi_path;
+
+/* Solve outcome. */
+typedef enum {
+  JACOBI_SOLVE_CONVERGED = 0,
+  JACOBI_SOLVE_MAX_ITERS = 1,
+  JACOBI_SOLVE_STAGNATED = 2
+} jacobi_solve_status;
+
+/* Copy layouts for jacobi_copy_out / jacobi_set_state. */
+enum { JACOBI_LAYOUT_INTERIOR = 0, JACOBI_LAYOUT_PADDED = 1 };
+
+typedef struct jacobi_s jacobi_t;
+typedef struct channel_s channel_t;
+
+/* Block description (host-side view of the decomposition). */
+typedef struct {
+  int64_t grid;          /* owning grid index within the handle         */
+  int64_t origin[3];     /* first interior point (x, y, z), 0-based      */
+  int64_t extent[3];     /* points per axis                              */
+  int64_t neighbour[6];  /* block id across face xm,xp,ym,yp,zm,zp, -1 = Dirichlet */
+} jacobi_block_info;
+
+typedef struct {
+  int64_t n_grids;
+  int64_t n_blocks;
+  int64_t n_points;      /* interior points over all grids             */
+  int64_t iteration;     /* iterations completed so far                */
+  int32_t dtype;
+  int32_t path;
+  int64_t halo_bytes_per_iter; /* face payload moved per iteration (bytes) */
+  size_t workspace_bytes;
+} jacobi_info_t;
+
+/* ---- errors -------------------------------------------------------------- */
+const char* jacobi_strerror(int code);
+/* Message of the last failing call on the calling thread ("" if none). */
+const char* jacobi_last_error(void);
+
+/* ---- decomposition (host only; no GPU needed) ------------------------------ */
+
+/* Block counts px*py*pz == nblocks, p <= n per axis, minimising the total
+ * block surface of the near-equal split (Sec. 4.3 chooses the cuboid split
+ * with the least surface, i.e. the least halo volume); ties go to the
+ * lexicographically smallest (px, py, pz).
+ * JACOBI_EINVAL if no split fits. */
+int jacobi_decompose(jacobi_dim3 grid, int64_t nblocks, jacobi_dim3* counts_out);
+
+/* Device bytes jacobi_create needs for one grid (states, receive slots,
+ * flags, tables, reduction partials), for a caller-supplied workspace. */
+int jacobi_workspace_bytes(jacobi_dim3 grid, jacobi_split split, jacobi_dtype dtype,
+                           size_t* bytes);
+int jacobi_workspace_bytes_batch(int64_t n_grids, const jacobi_dim3* grids,
+                                 const jacobi_split* splits, jacobi_dtype dtype,
+                                 size_t* bytes);
+
+/* ---- lifecycle ------------------------------------------------------------- */
+
+/* Create a solver for one grid.  `init` may be NULL (linear boundary, zero
+ * interior).  `workspace` may be NULL (the library allocates and frees it)
+ * or a device buffer of at least jacobi_workspace_bytes() bytes, 256-byte
+ * aligned, owned by the caller.  The initial state is written by a kernel on
+ * `stream`; the call returns without waiting for it. */
+int jacobi_create(jacobi_dim3 grid, jacobi_split split, jacobi_dtype dtype,
+                  const jacobi_init* init, void* workspace, size_t ws_bytes, void* stream,
+                  jacobi_t** out);
+
+/* Create one handle holding n_grids independent grids (batched stepping:
+ * every grid advances in the same launches).  grids/splits/inits are arrays of
+ * n_grids entries (inits may be NULL). */
+int jacobi_create_batch(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* splits,
+                        jacobi_dtype dtype, const jacobi_init* inits, void* workspace,
+                        size_t ws_bytes, void* stream, jacobi_t** out);
+
+/* Waits for the handle's outstanding work, then frees what the library
+ * allocated (never the caller's workspace). */
+int jacobi_destroy(jacobi_t* h);
+
+int jacobi_info(const jacobi_t* h, jacobi_info_t* out);
+int jacobi_block(const jacobi_t* h, int64_t block, jacobi_block_info* out);
+
+/* Select the step path (jacobi_path).  PERSISTENT fails with JACOBI_EINVAL at
+ * the next step if the blocks cannot all be co-resident on the GPU. */
+int jacobi_set_path(jacobi_t* h, int32_t path);
+
+/* ---- state transfer ---------------------------------------------------------- */
+
+/* Replace the whole state of grid `grid` (boundary and interior) from a padded
+ * array (src_on_device: 0 = host memory, 1 = device memory) of the handle's
+ * dtype.  Host sources are copied synchronously; device sources are read on
+ * `stream`.  Resets nothing else: the iteration counter keeps counting. */
+int jacobi_set_state(jacobi_t* h, int64_t grid, const void* src, int32_t src_on_device,
+                     void* stream);
+
+/* Copy grid `grid`'s current iterate out in the interior or padded layout
+ * (dtype of the handle).  dst_on_device = 0 (host; the call synchronises the
+ * stream) or 1 (device; asynchronous). */
+int jacobi_copy_out(jacobi_t* h, int64_t grid, void* dst, int32_t dst_on_device, int32_t layout,
+                    void* stream);
+
+/* ---- the hot path ------------------------------------------------------------ */
+
+/* Advance every grid of the handle by n_iters Jacobi iterations (Sec. 4.3),
+ * halo exchange included, on the selected path.  Asynchronous. */
+int jacobi_step(jacobi_t* h, int64_t n_iters, void* stream);
+
+/* FP64 residual of the current iterate of every grid: rel[g] = |b-Au|/|b|,
+ * abs[g] = |b-Au| (either pointer may be NULL; arrays of n_grids doubles in
+ * host memory).  Partials are reduced in a fixed order, so results are
+ * reproducible bit for bit.  Synchronises the stream. */
+int jacobi_residual(jacobi_t* h, double* rel, double* abs_res, void* stream);
+
+/* Iterate until rel <= tol for every grid, checking every check_every
+ * iterations on the current iterate (the residual of u_k is fused into the
+ * step that computes u_{k+1}); a grid whose check passes is frozen at u_k.
+ * Stops at max_iters (status MAX_ITERS) or after stall_checks (> 0) checks
+ * without a new best rel (STAGNATED).  Per-grid outputs (host arrays of
+ * n_grids entries, NULL allowed): iterations done, rel at stop, status.
+ * Synchronises the stream once per check. */
+int jacobi_solve(jacobi_t* h, double tol, int64_t max_iters, int64_t check_every,
+                 int64_t stall_checks, int64_t* iters_out, double* rel_out, int32_t* status_out,
+                 void* stream);
+
+/* Synchronise `stream` and report the first device-side failure of the
+ * handle's persistent steps (JACOBI_ETIMEDOUT when a bounded neighbour wait
+ * expired) or JACOBI_OK; clears it. */
+int jacobi_sync(jacobi_t* h, void* stream);
+
+/* Copy the receive slot that block `block` reads across face `face`
+ * (0..5 = xm, xp, ym, yp, zm, zp) at its next iteration into host memory
+ * `dst` (face layout: x-faces [z][y], y-faces [z][x], z-faces [y][x]; handle
+ * dtype).  After a step this is the neighbour's packed boundary plane (or the
+ * Dirichlet boundary).  Synchronises the stream. */
+int jacobi_read_face(jacobi_t* h, int64_t block, int32_t face, void* dst, void* stream);
+
+/* Host-side fault injection for tests: the next persistent steps leave block
+ * `block` out of the launch (its sends never happen), so its neighbours'
+ * bounded waits expire and jacobi_sync reports JACOBI_ETIMEDOUT.  block = -1
+ * clears the injection. */
+int jacobi_debug_drop_block(jacobi_t* h, int64_t block);
+
+/* ---- channels (Sec. 3.1 tag scheme, Sec. 3.2.2 Channel API) ------------------ */
+
+/* Open a two-sided channel between blocks a and b with a caller-chosen id
+ * that is unique within the handle (Sec. 3.2.2).  The library allocates, for
+ * each endpoint, two receive slots of max_bytes (parity double buffering),
+ * plus per-endpoint message counters in device memory: a message's sequence
+ * number plays the role of the 32-bit per-endpoint counter of the paper's
+ * channel tag (Sec. 3.1), so messages are matched in order and exactly once. */
+int channel_open(jacobi_t* h, uint32_t channel_id, int64_t block_a, int64_t block_b,
+                 size_t max_bytes, channel_t** out);
+
+/* Send `bytes` from device buffer src (16-byte aligned) on behalf of endpoint
+ * `from_block` into the peer's receive slot, then publish the message's
+ * sequence number with a release store.  Waits on the device (bounded) until
+ * the peer has consumed the message that used the same slot two sends ago.
+ * Asynchronous; a failed wait is reported by channel_sync. */
+int channel_send(channel_t* ch, int64_t from_block, const void* src, size_t bytes, void* stream);
+
+/* Receive the next message for endpoint `at_block`: acquire-wait (bounded)
+ * until its sequence number is published, copy it to dst (device, 16-byte
+ * aligned), or leave it in the slot when dst is NULL (zero-copy; see
+ * channel_slot), then mark it consumed.  `bytes` must equal the sent size
+ * (JACOBI_ESEQ otherwise, reported by channel_sync).  Asynchronous.  A receive
+ * with no matching send in stream order times out with JACOBI_ETIMEDOUT. */
+int channel_recv(channel_t* ch, int64_t at_block, void* dst, size_t bytes, void* stream);
+
+/* Device address of endpoint at_block's receive slot for message parity
+ * `parity` (message n uses parity n & 1). */
+int channel_slot(channel_t* ch, int64_t at_block, int32_t parity, void** slot);
+
+/* Synchronise `stream` and report the first device-side failure of the
+ * channel (JACOBI_ETIMEDOUT, JACOBI_ESEQ) or JACOBI_OK; clears it. */
+int channel_sync(channel_t* ch, void* stream);
+
+/* OSU-style ping-pong between the two endpoints (Sec. 4.2.1), run entirely on
+ * the device: one cooperative launch whose first `ctas_per_side` CTAs act as
+ * endpoint a and the rest as endpoint b; each round trip sends `bytes` a->b
+ * and back through the channel's slots and counters.  The caller times the
+ * launch with events on `stream`; one-way latency = elapsed / (2*round_trips). */
+int channel_pingpong(channel_t* ch, size_t bytes, int64_t round_trips, int32_t ctas_per_side,
+                     void* stream);
+
+int channel_close(channel_t* ch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JACOBI_H */

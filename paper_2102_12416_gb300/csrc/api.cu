@@ -1,0 +1,866 @@
+// C ABI of the Jacobi3D library: decomposition (Sec. 4.3: equal-size cuboid
+// blocks that minimise surface area), workspace planning, handle lifecycle,
+// the step paths, residual / solve and state transfer.  Every numeric step
+// runs in the kernels of kernels.cu; this file only plans, uploads tables and
+// launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "runtime.h"
+
+using namespace jgb;
+
+namespace jgb {
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+// Per-axis (origin, extent) of a split.
+static int axis_split(int64_t n, int32_t mode, int64_t param, std::vector<std::pair<int64_t, int64_t>>* out) {
+  out->clear();
+  if (n < 1 || param < 1) return set_error(JACOBI_EINVAL, "grid and split sizes must be positive");
+  if (mode == JACOBI_SPLIT_SHAPE) {
+    for (int64_t o = 0; o < n; o += param) out->push_back({o, std::min(param, n - o)});
+  } else if (mode == JACOBI_SPLIT_COUNT) {
+    if (param > n) return set_error(JACOBI_EINVAL, "more blocks (%lld) than points (%lld) on an axis",
+                                    (long long)param, (long long)n);
+    const int64_t q = n / param, r = n % param;
+    int64_t o = 0;
+    for (int64_t b = 0; b < param; ++b) {
+      const int64_t e = q + (b < r ? 1 : 0);
+      out->push_back({o, e});
+      o += e;
+    }
+  } else {
+    return set_error(JACOBI_EINVAL, "unknown split mode %d", mode);
+  }
+  return JACOBI_OK;
+}
+
+static int64_t face_elems_host(const BlockHost& b, int f) {
+  if (f < 2) return b.extent[1] * b.extent[2];
+  if (f < 4) return b.extent[0] * b.extent[2];
+  return b.extent[0] * b.extent[1];
+}
+
+int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* splits, jacobi_dtype dtype,
+               const jacobi_init* inits, Plan* P) {
+  if (n_grids < 1 || !grids || !splits) return set_error(JACOBI_EINVAL, "need at least one grid");
+  if (dtype != JACOBI_F64 && dtype != JACOBI_F32) return set_error(JACOBI_EINVAL, "bad dtype %d", (int)dtype);
+  *P = Plan();
+  P->dtype = dtype;
+  P->elem = dtype == JACOBI_F64 ? 8 : 4;
+  const size_t A = 256;
+  for (int64_t g = 0; g < n_grids; ++g) {
+    const jacobi_dim3 d = grids[g];
+    if (d.nx < 1 || d.ny < 1 || d.nz < 1 || d.nx > (1ll << 30) || d.ny > (1ll << 30) || d.nz > (1ll << 30))
+      return set_error(JACOBI_EINVAL, "grid %lld: bad size %lldx%lldx%lld", (long long)g, (long long)d.nx,
+                       (long long)d.ny, (long long)d.nz);
+    std::vector<std::pair<int64_t, int64_t>> ax[3];
+    const int64_t n3[3] = {d.nx, d.ny, d.nz};
+    const int64_t s3[3] = {splits[g].x, splits[g].y, splits[g].z};
+    for (int a = 0; a < 3; ++a) {
+      int rc = axis_split(n3[a], splits[g].mode, s3[a], &ax[a]);
+      if (rc) return rc;
+      for (auto& pe : ax[a])
+        if (pe.second > 32767) return set_error(JACOBI_EINVAL, "block extent %lld exceeds 32767", (long long)pe.second);
+    }
+    GridHost G;
+    G.dims = d;
+    G.split = splits[g];
+    if (inits) {
+      G.init = inits[g];
+    } else {
+      G.init = jacobi_init{JACOBI_BC_LINEAR, JACOBI_INTERIOR_ZERO, 0, 0, 0.0};
+    }
+    if (G.init.bc < 0 || G.init.bc > 2 || G.init.interior < 0 || G.init.interior > 2)
+      return set_error(JACOBI_EINVAL, "grid %lld: bad init", (long long)g);
+    G.counts[0] = (int64_t)ax[0].size();
+    G.counts[1] = (int64_t)ax[1].size();
+    G.counts[2] = (int64_t)ax[2].size();
+    G.block_begin = (int64_t)P->blocks.size();
+    G.start_iter = 0;
+    G.frozen_local = 0;
+    G.active = true;
+    const int64_t px = G.counts[0], py = G.counts[1], pz = G.counts[2];
+    for (int64_t bz = 0; bz < pz; ++bz)
+      for (int64_t by = 0; by < py; ++by)
+        for (int64_t bx = 0; bx < px; ++bx) {
+          BlockHost B{};
+          B.grid = g;
+          B.origin[0] = ax[0][bx].first; B.extent[0] = ax[0][bx].second;
+          B.origin[1] = ax[1][by].first; B.extent[1] = ax[1][by].second;
+          B.origin[2] = ax[2][bz].first; B.extent[2] = ax[2][bz].second;
+          auto id = [&](int64_t x, int64_t y, int64_t z) { return G.block_begin + (z * py + y) * px + x; };
+          B.nbr[XM] = bx > 0 ? id(bx - 1, by, bz) : -1;
+          B.nbr[XP] = bx + 1 < px ? id(bx + 1, by, bz) : -1;
+          B.nbr[YM] = by > 0 ? id(bx, by - 1, bz) : -1;
+          B.nbr[YP] = by + 1 < py ? id(bx, by + 1, bz) : -1;
+          B.nbr[ZM] = bz > 0 ? id(bx, by, bz - 1) : -1;
+          B.nbr[ZP] = bz + 1 < pz ? id(bx, by, bz + 1) : -1;
+          P->blocks.push_back(B);
+        }
+    G.block_end = (int64_t)P->blocks.size();
+    if (G.block_end > (1ll << 30)) return set_error(JACOBI_EINVAL, "too many blocks");
+    // Work items of this grid: tiles of TX x TY columns; the z-chunk depends
+    // only on this grid, so a grid's items (and its residual summation order)
+    // are the same alone or in a batch.
+    int64_t tiles = 0, maxz = 0;
+    for (int64_t b = G.block_begin; b < G.block_end; ++b) {
+      const BlockHost& B = P->blocks[b];
+      tiles += ((B.extent[0] + TX - 1) / TX) * ((B.extent[1] + TY - 1) / TY);
+      maxz = std::max(maxz, B.extent[2]);
+    }
+    int64_t zc = maxz;
+    while (zc > 8 && tiles * ((maxz + zc - 1) / zc) < 1024) zc = (zc + 1) / 2;
+    G.item_begin = (int64_t)P->items.size();
+    for (int64_t b = G.block_begin; b < G.block_end; ++b) {
+      BlockHost& B = P->blocks[b];
+      B.item_begin = (int64_t)P->items.size();
+      for (int64_t z0 = 0; z0 < B.extent[2]; z0 += zc)
+        for (int64_t y0 = 0; y0 < B.extent[1]; y0 += TY)
+          for (int64_t x0 = 0; x0 < B.extent[0]; x0 += TX) {
+            WorkItem w;
+            w.block = (int32_t)b;
+            w.slot = (int32_t)P->items.size();
+            w.x0 = (int16_t)x0;
+            w.y0 = (int16_t)y0;
+            w.z0 = (int16_t)z0;
+            w.z1 = (int16_t)std::min(B.extent[2], z0 + zc);
+            P->items.push_back(w);
+          }
+      B.item_end = (int64_t)P->items.size();
+    }
+    G.item_end = (int64_t)P->items.size();
+    if (G.item_end > (1ll << 30)) return set_error(JACOBI_EINVAL, "too many work items");
+    P->n_points += d.nx * d.ny * d.nz;
+    P->grids.push_back(G);
+  }
+  const int64_t nb = (int64_t)P->blocks.size(), ni = (int64_t)P->items.size(), ng = n_grids;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, A); return o; };
+  P->off_blocks = take(nb * sizeof(BlockDev));
+  P->off_geom = take(nb * sizeof(BlockGeom));
+  P->off_items = take(ni * sizeof(WorkItem));
+  P->off_active = take(ni * sizeof(WorkItem));
+  P->off_grids = take(ng * sizeof(GridDev));
+  P->off_norms = take(ng * sizeof(GridNorm));
+  P->off_inits = take(ng * sizeof(InitDev));
+  P->off_gids = take(ng * sizeof(int32_t));
+  P->off_partials = take(ni * sizeof(double));
+  P->off_progress = take(nb * sizeof(int64_t));
+  P->off_err = take(64);
+  P->off_stage_tab = take(nb * 6 * sizeof(void*));
+  P->off_pblock_items = take((nb + 1) * sizeof(int32_t));
+  P->off_pblock_ids = take(nb * sizeof(int32_t));
+  const size_t per16 = 32;  // plane pitch rounded to 32 elements
+  for (auto& B : P->blocks) {
+    B.pitch = (int64_t)align_up((size_t)(B.extent[0] * B.extent[1]), per16);
+    const size_t sb = (size_t)B.pitch * B.extent[2] * P->elem;
+    B.u_off[0] = take(sb);
+    B.u_off[1] = take(sb);
+  }
+  for (auto& B : P->blocks) {
+    for (int f = 0; f < 6; ++f) {
+      const size_t fb = (size_t)face_elems_host(B, f) * P->elem;
+      if (B.nbr[f] >= 0) {
+        B.recv_off[f][0] = take(fb);
+        B.recv_off[f][1] = take(fb);
+        P->halo_elems += face_elems_host(B, f);
+      } else {
+        B.recv_off[f][0] = B.recv_off[f][1] = take(fb);
+      }
+    }
+  }
+  for (auto& B : P->blocks)
+    for (int f = 0; f < 6; ++f)
+      B.stage_off[f] = B.nbr[f] >= 0 ? take((size_t)face_elems_host(B, f) * P->elem) : 0;
+  P->bytes = off;
+  return JACOBI_OK;
+}
+
+}  // namespace jgb
+
+// ---------------------------------------------------------------------------
+// internal helpers
+// ---------------------------------------------------------------------------
+namespace {
+
+cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+int upload_tables(jacobi_t* h, cudaStream_t s) {
+  const Plan& P = h->plan;
+  const int64_t nb = (int64_t)P.blocks.size();
+  std::vector<BlockDev> bd(nb);
+  std::vector<BlockGeom> geo(nb);
+  std::vector<void*> stab(nb * 6, nullptr);
+  for (int64_t b = 0; b < nb; ++b) {
+    const BlockHost& B = P.blocks[b];
+    BlockDev& D = bd[b];
+    memset(&D, 0, sizeof D);
+    D.u[0] = h->ws + B.u_off[0];
+    D.u[1] = h->ws + B.u_off[1];
+    for (int f = 0; f < 6; ++f) {
+      D.recv[f][0] = h->ws + B.recv_off[f][0];
+      D.recv[f][1] = h->ws + B.recv_off[f][1];
+      D.nbr[f] = (int32_t)B.nbr[f];
+      if (B.nbr[f] >= 0) {
+        const BlockHost& N = P.blocks[B.nbr[f]];
+        D.send[f][0] = h->ws + N.recv_off[opposite(f)][0];
+        D.send[f][1] = h->ws + N.recv_off[opposite(f)][1];
+        stab[b * 6 + f] = h->ws + B.stage_off[f];
+      }
+    }
+    D.nx = (int32_t)B.extent[0];
+    D.ny = (int32_t)B.extent[1];
+    D.nz = (int32_t)B.extent[2];
+    D.grid = (int32_t)B.grid;
+    D.plane_pitch = B.pitch;
+    geo[b] = BlockGeom{(int32_t)B.origin[0], (int32_t)B.origin[1], (int32_t)B.origin[2], (int32_t)B.grid};
+  }
+  const int64_t ng = (int64_t)P.grids.size();
+  std::vector<InitDev> ini(ng);
+  std::vector<int32_t> gids(ng);
+  for (int64_t g = 0; g < ng; ++g) {
+    const GridHost& G = P.grids[g];
+    ini[g] = InitDev{G.dims.nx, G.dims.ny, G.dims.nz, G.init.bc, G.init.interior, G.init.bc_seed,
+                     G.init.interior_seed, G.init.noise_amp};
+    gids[g] = (int32_t)g;
+    GridDev& D = h->h_grids[g];
+    D.start_iter = G.start_iter;
+    D.item_begin = (int32_t)G.item_begin;
+    D.item_end = (int32_t)G.item_end;
+  }
+  JGB_CUDA(cudaMemcpyAsync(h->d_blocks, bd.data(), nb * sizeof(BlockDev), cudaMemcpyHostToDevice, s));
+  JGB_CUDA(cudaMemcpyAsync(h->d_geom, geo.data(), nb * sizeof(BlockGeom), cudaMemcpyHostToDevice, s));
+  JGB_CUDA(cudaMemcpyAsync(h->d_items, P.items.data(), P.items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
+  JGB_CUDA(cudaMemcpyAsync(h->d_inits, ini.data(), ng * sizeof(InitDev), cudaMemcpyHostToDevice, s));
+  JGB_CUDA(cudaMemcpyAsync(h->d_gids, gids.data(), ng * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  JGB_CUDA(cudaMemcpyAsync(h->d_stage_tab, stab.data(), stab.size() * sizeof(void*), cudaMemcpyHostToDevice, s));
+  JGB_CUDA(cudaMemcpyAsync(h->d_grids, h->h_grids, ng * sizeof(GridDev), cudaMemcpyHostToDevice, s));
+  JGB_CUDA(cudaMemsetAsync(h->d_norms, 0, ng * sizeof(GridNorm), s));
+  JGB_CUDA(cudaMemsetAsync(h->d_progress, 0, nb * sizeof(int64_t), s));
+  JGB_CUDA(cudaMemsetAsync(h->d_err, 0, 64, s));
+  // The host arrays above are pageable, so each copy has been staged before
+  // cudaMemcpyAsync returned; they may go out of scope now.
+  return JACOBI_OK;
+}
+
+// Rebuild the active item / block lists from the grids' active flags.
+int refresh_active(jacobi_t* h, cudaStream_t s) {
+  if (!h->tables_dirty) return JACOBI_OK;
+  const Plan& P = h->plan;
+  h->active_items.clear();
+  h->active_blocks.clear();
+  h->active_block_items.clear();
+  h->active_grids.clear();
+  for (size_t g = 0; g < P.grids.size(); ++g) {
+    const GridHost& G = P.grids[g];
+    if (!G.active) continue;
+    h->active_grids.push_back((int32_t)g);
+    for (int64_t b = G.block_begin; b < G.block_end; ++b) {
+      if (b == h->drop_block && h->path == JACOBI_PATH_PERSISTENT) continue;  // injected fault
+      h->active_blocks.push_back((int32_t)b);
+      h->active_block_items.push_back((int32_t)h->active_items.size());
+      const BlockHost& B = P.blocks[b];
+      for (int64_t q = B.item_begin; q < B.item_end; ++q) h->active_items.push_back(P.items[q]);
+    }
+  }
+  h->active_block_items.push_back((int32_t)h->active_items.size());
+  if (!h->active_items.empty())
+    JGB_CUDA(cudaMemcpyAsync(h->d_active, h->active_items.data(), h->active_items.size() * sizeof(WorkItem),
+                             cudaMemcpyHostToDevice, s));
+  if (!h->active_blocks.empty()) {
+    JGB_CUDA(cudaMemcpyAsync(h->d_pblock_ids, h->active_blocks.data(), h->active_blocks.size() * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, s));
+    JGB_CUDA(cudaMemcpyAsync(h->d_pblock_items, h->active_block_items.data(),
+                             h->active_block_items.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  }
+  // start_iter of every grid (changes when grids are frozen / re-activated)
+  for (size_t g = 0; g < P.grids.size(); ++g) h->h_grids[g].start_iter = P.grids[g].start_iter;
+  JGB_CUDA(cudaMemcpyAsync(h->d_grids, h->h_grids, P.grids.size() * sizeof(GridDev), cudaMemcpyHostToDevice, s));
+  JGB_CUDA(cudaStreamSynchronize(s));  // host mirrors are reused below
+  h->tables_dirty = false;
+  return JACOBI_OK;
+}
+
+StepLaunch step_args(jacobi_t* h, int64_t it, bool all_items) {
+  StepLaunch a;
+  a.blocks = h->d_blocks;
+  a.items = all_items ? h->d_items : h->d_active;
+  a.n_items = all_items ? (int32_t)h->plan.items.size() : (int32_t)h->active_items.size();
+  a.grids = h->d_grids;
+  a.it = it;
+  a.partials = h->d_partials;
+  a.dtype = h->plan.dtype;
+  return a;
+}
+
+int check_err_word(jacobi_t* h, cudaStream_t s) {
+  JGB_CUDA(cudaMemcpyAsync(h->h_err, h->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  JGB_CUDA(cudaStreamSynchronize(s));
+  if (*h->h_err != DEV_OK) {
+    const uint32_t e = *h->h_err;
+    JGB_CUDA(cudaMemsetAsync(h->d_err, 0, sizeof(uint32_t), s));
+    JGB_CUDA(cudaStreamSynchronize(s));
+    return set_error(e == DEV_TIMEOUT ? JACOBI_ETIMEDOUT : JACOBI_ESEQ,
+                     "device-side wait failed (code %u) in the persistent step", e);
+  }
+  return JACOBI_OK;
+}
+
+int step_fused_direct(jacobi_t* h, int64_t it0, int64_t n, cudaStream_t s) {
+  StepLaunch a = step_args(h, 0, false);
+  for (int64_t t = 0; t < n; ++t) {
+    a.it = it0 + t;
+    JGB_CUDA(launch_step(a, kWrite | kPack, s));
+  }
+  return JACOBI_OK;
+}
+
+int step_graph(jacobi_t* h, int64_t it0, int64_t n, cudaStream_t s) {
+  const int64_t K = 32;  // iterations per graph replay (even, so parity repeats)
+  int64_t done = 0;
+  if ((it0 & 1) && n > 0) {
+    int rc = step_fused_direct(h, it0, 1, s);
+    if (rc) return rc;
+    done = 1;
+  }
+  if (n - done >= K) {
+    if (!h->graph || h->graph_items != (int32_t)h->active_items.size()) {
+      if (h->graph) cudaGraphExecDestroy(h->graph);
+      h->graph = nullptr;
+      cudaStream_t cs;
+      JGB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        StepLaunch a = step_args(h, 0, false);
+        for (int64_t t = 0; t < K && e == cudaSuccess; ++t) {
+          a.it = t;
+          e = launch_step(a, kWrite | kPack, cs);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = e2;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph, g, 0);
+      if (g) cudaGraphDestroy(g);
+      cudaStreamDestroy(cs);
+      if (e != cudaSuccess) return set_error(JACOBI_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+      h->graph_items = (int32_t)h->active_items.size();
+      h->graph_iters = K;
+    }
+    while (n - done >= K) {
+      JGB_CUDA(cudaGraphLaunch(h->graph, s));
+      done += K;
+    }
+  }
+  return step_fused_direct(h, it0 + done, n - done, s);
+}
+
+int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaStream_t s) {
+  const int maxc = persistent_max_ctas(h->plan.dtype);
+  if (maxc <= 0) return set_error(JACOBI_ECUDA, "occupancy query for the persistent kernel failed");
+  PersistLaunch a;
+  a.blocks = h->d_blocks;
+  a.items = h->d_active;
+  a.block_items = h->d_pblock_items;
+  a.block_ids = h->d_pblock_ids;
+  a.n_blocks = (int32_t)h->active_blocks.size();
+  a.grids = h->d_grids;
+  a.it0 = it0;
+  a.n_iters = n;
+  a.progress = h->d_progress;
+  a.err = h->d_err;
+  a.wait_ns = h->wait_ns;
+  a.partials = h->d_partials;
+  a.resid_first = resid_first ? 1 : 0;
+  a.dtype = h->plan.dtype;
+  const int ctas = std::min(maxc, a.n_blocks);
+  JGB_CUDA(launch_persistent(a, ctas, s));
+  return JACOBI_OK;
+}
+
+int step_explicit(jacobi_t* h, int64_t it0, int64_t n, cudaStream_t s) {
+  StepLaunch a = step_args(h, 0, false);
+  const int32_t nb = (int32_t)h->plan.blocks.size();
+  for (int64_t t = 0; t < n; ++t) {
+    a.it = it0 + t;
+    JGB_CUDA(launch_step(a, kWrite, s));
+    JGB_CUDA(launch_pack_faces(h->d_blocks, nb, h->d_stage_tab, h->d_grids, a.it, h->plan.dtype, s));
+    JGB_CUDA(launch_copy_faces(h->d_blocks, nb, h->d_stage_tab, h->d_grids, a.it, h->plan.dtype, s));
+  }
+  return JACOBI_OK;
+}
+
+// Advance active grids by n iterations on the selected path.
+int do_step(jacobi_t* h, int64_t n, cudaStream_t s) {
+  int rc = refresh_active(h, s);
+  if (rc) return rc;
+  if (n <= 0 || h->active_items.empty()) {
+    h->iter += std::max<int64_t>(n, 0);
+    return JACOBI_OK;
+  }
+  switch (h->path) {
+    case JACOBI_PATH_FUSED: rc = step_fused_direct(h, h->iter, n, s); break;
+    case JACOBI_PATH_GRAPH: rc = step_graph(h, h->iter, n, s); break;
+    case JACOBI_PATH_PERSISTENT: rc = step_persistent(h, h->iter, n, false, s); break;
+    case JACOBI_PATH_EXPLICIT: rc = step_explicit(h, h->iter, n, s); break;
+    default: return set_error(JACOBI_EINVAL, "bad path");
+  }
+  if (rc) return rc;
+  h->iter += n;
+  return JACOBI_OK;
+}
+
+// One step that also produces the residual of the current iterate (fused),
+// followed by the per-grid reduction.  Does not synchronise.
+int step_with_residual(jacobi_t* h, cudaStream_t s) {
+  int rc = refresh_active(h, s);
+  if (rc) return rc;
+  if (h->path == JACOBI_PATH_PERSISTENT) {
+    rc = step_persistent(h, h->iter, 1, true, s);
+    if (rc) return rc;
+  } else {
+    StepLaunch a = step_args(h, h->iter, false);
+    JGB_CUDA(launch_step(a, kWrite | kPack | kResid, s));
+    if (h->path == JACOBI_PATH_EXPLICIT) {
+      // the fused pack already delivered the faces; nothing else to move
+    }
+  }
+  JGB_CUDA(launch_reduce(h->d_grids, h->d_norms, h->d_gids, (int32_t)h->plan.grids.size(), h->d_partials, 0, s));
+  h->iter += 1;
+  return JACOBI_OK;
+}
+
+int residual_only(jacobi_t* h, cudaStream_t s) {
+  int rc = refresh_active(h, s);
+  if (rc) return rc;
+  StepLaunch a = step_args(h, h->iter, false);
+  JGB_CUDA(launch_step(a, kResid, s));
+  JGB_CUDA(launch_reduce(h->d_grids, h->d_norms, h->d_gids, (int32_t)h->plan.grids.size(), h->d_partials, 0, s));
+  return JACOBI_OK;
+}
+
+int compute_bnorm(jacobi_t* h, cudaStream_t s) {
+  StepLaunch a = step_args(h, h->iter, true);
+  JGB_CUDA(launch_bnorm(a, s));
+  JGB_CUDA(launch_reduce(h->d_grids, h->d_norms, h->d_gids, (int32_t)h->plan.grids.size(), h->d_partials, 1, s));
+  return JACOBI_OK;
+}
+
+int read_norms(jacobi_t* h, cudaStream_t s) {
+  JGB_CUDA(cudaMemcpyAsync(h->h_norms, h->d_norms, h->plan.grids.size() * sizeof(GridNorm), cudaMemcpyDeviceToHost, s));
+  JGB_CUDA(cudaStreamSynchronize(s));
+  return JACOBI_OK;
+}
+
+int stage_get(jacobi_t* h, size_t bytes, void** out) {
+  if (h->stage_bytes < bytes) {
+    if (h->stage) cudaFree(h->stage);
+    h->stage = nullptr;
+    h->stage_bytes = 0;
+    JGB_CUDA(cudaMalloc(&h->stage, bytes));
+    h->stage_bytes = bytes;
+  }
+  *out = h->stage;
+  return JACOBI_OK;
+}
+
+int64_t grid_local_iter(const jacobi_t* h, int64_t g) {
+  const GridHost& G = h->plan.grids[g];
+  return G.active ? h->iter - G.start_iter : G.frozen_local;
+}
+
+void freeze_grid(jacobi_t* h, int64_t g, int64_t local) {
+  GridHost& G = h->plan.grids[g];
+  G.frozen_local = local;
+  G.active = false;
+  h->tables_dirty = true;
+}
+
+void activate_grid(jacobi_t* h, int64_t g) {
+  GridHost& G = h->plan.grids[g];
+  if (G.active) return;
+  G.start_iter = h->iter - G.frozen_local;
+  G.active = true;
+  h->tables_dirty = true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* jacobi_strerror(int code) {
+  switch (code) {
+    case JACOBI_OK: return "ok";
+    case JACOBI_EINVAL: return "invalid argument";
+    case JACOBI_ENOMEM: return "out of memory";
+    case JACOBI_EBUSY: return "busy";
+    case JACOBI_EAGAIN: return "not ready";
+    case JACOBI_ETIMEDOUT: return "device wait timed out";
+    case JACOBI_ECUDA: return "CUDA error";
+    case JACOBI_ESEQ: return "channel sequence mismatch";
+    default: return "unknown error";
+  }
+}
+
+const char* jacobi_last_error(void) { return jgb::g_last_error.c_str(); }
+
+int jacobi_decompose(jacobi_dim3 grid, int64_t nblocks, jacobi_dim3* out) {
+  if (!out || nblocks < 1 || grid.nx < 1 || grid.ny < 1 || grid.nz < 1)
+    return set_error(JACOBI_EINVAL, "bad arguments to jacobi_decompose");
+  // Total block surface of a near-equal split: sum over blocks of
+  // 2(ex*ey + ey*ez + ez*ex) = 2(nx*ny*pz + ny*nz*px + nz*nx*py).
+  bool found = false;
+  int64_t best = 0;
+  jacobi_dim3 arg{0, 0, 0};
+  for (int64_t px = 1; px <= nblocks; ++px) {
+    if (nblocks % px) continue;
+    for (int64_t py = 1; py <= nblocks / px; ++py) {
+      if ((nblocks / px) % py) continue;
+      const int64_t pz = nblocks / px / py;
+      if (px > grid.nx || py > grid.ny || pz > grid.nz) continue;
+      const int64_t area = 2 * (grid.nx * grid.ny * pz + grid.ny * grid.nz * px + grid.nz * grid.nx * py);
+      if (!found || area < best) {  // loop order is lexicographic, so ties keep the first
+        found = true;
+        best = area;
+        arg = jacobi_dim3{px, py, pz};
+      }
+    }
+  }
+  if (!found) return set_error(JACOBI_EINVAL, "no split of %lld blocks fits the grid", (long long)nblocks);
+  *out = arg;
+  return JACOBI_OK;
+}
+
+int jacobi_workspace_bytes_batch(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* splits,
+                                 jacobi_dtype dtype, size_t* bytes) {
+  if (!bytes) return set_error(JACOBI_EINVAL, "bytes is null");
+  Plan P;
+  int rc = plan_build(n_grids, grids, splits, dtype, nullptr, &P);
+  if (rc) return rc;
+  *bytes = P.bytes;
+  return JACOBI_OK;
+}
+
+int jacobi_workspace_bytes(jacobi_dim3 grid, jacobi_split split, jacobi_dtype dtype, size_t* bytes) {
+  return jacobi_workspace_bytes_batch(1, &grid, &split, dtype, bytes);
+}
+
+int jacobi_create_batch(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* splits, jacobi_dtype dtype,
+                        const jacobi_init* inits, void* workspace, size_t ws_bytes, void* stream, jacobi_t** out) {
+  if (!out) return set_error(JACOBI_EINVAL, "out is null");
+  *out = nullptr;
+  jacobi_t* h = new (std::nothrow) jacobi_t();
+  if (!h) return set_error(JACOBI_ENOMEM, "host allocation failed");
+  int rc = plan_build(n_grids, grids, splits, dtype, inits, &h->plan);
+  if (rc) {
+    delete h;
+    return rc;
+  }
+  const cudaStream_t s = S(stream);
+  auto fail = [&](int code) {
+    if (h->own_ws && h->ws) cudaFree(h->ws);
+    if (h->h_grids) cudaFreeHost(h->h_grids);
+    if (h->h_norms) cudaFreeHost(h->h_norms);
+    if (h->h_err) cudaFreeHost(h->h_err);
+    delete h;
+    return code;
+  };
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) return fail(set_error(JACOBI_ECUDA, "no CUDA device: %s", cudaGetErrorString(e)));
+  if (workspace) {
+    if (ws_bytes < h->plan.bytes)
+      return fail(set_error(JACOBI_ENOMEM, "workspace too small: %zu < %zu bytes", ws_bytes, h->plan.bytes));
+    if ((uintptr_t)workspace % 256) return fail(set_error(JACOBI_EINVAL, "workspace must be 256-byte aligned"));
+    h->ws = (char*)workspace;
+  } else {
+    e = cudaMalloc((void**)&h->ws, h->plan.bytes);
+    if (e != cudaSuccess) {
+      h->ws = nullptr;
+      return fail(set_error(JACOBI_ENOMEM, "cudaMalloc(%zu) failed: %s", h->plan.bytes, cudaGetErrorString(e)));
+    }
+    h->own_ws = true;
+  }
+  if (cudaMallocHost((void**)&h->h_grids, h->plan.grids.size() * sizeof(GridDev)) != cudaSuccess ||
+      cudaMallocHost((void**)&h->h_norms, h->plan.grids.size() * sizeof(GridNorm)) != cudaSuccess ||
+      cudaMallocHost((void**)&h->h_err, 64) != cudaSuccess)
+    return fail(set_error(JACOBI_ENOMEM, "pinned host allocation failed"));
+  const Plan& P = h->plan;
+  h->d_blocks = (BlockDev*)(h->ws + P.off_blocks);
+  h->d_geom = (BlockGeom*)(h->ws + P.off_geom);
+  h->d_items = (WorkItem*)(h->ws + P.off_items);
+  h->d_active = (WorkItem*)(h->ws + P.off_active);
+  h->d_grids = (GridDev*)(h->ws + P.off_grids);
+  h->d_norms = (GridNorm*)(h->ws + P.off_norms);
+  h->d_inits = (InitDev*)(h->ws + P.off_inits);
+  h->d_gids = (int32_t*)(h->ws + P.off_gids);
+  h->d_partials = (double*)(h->ws + P.off_partials);
+  h->d_progress = (int64_t*)(h->ws + P.off_progress);
+  h->d_err = (uint32_t*)(h->ws + P.off_err);
+  h->d_stage_tab = (void**)(h->ws + P.off_stage_tab);
+  h->d_pblock_items = (int32_t*)(h->ws + P.off_pblock_items);
+  h->d_pblock_ids = (int32_t*)(h->ws + P.off_pblock_ids);
+  if (const char* w = getenv("JACOBI_WAIT_MS")) {
+    const double ms = atof(w);
+    if (ms > 0) h->wait_ns = (uint64_t)(ms * 1e6);
+  }
+  rc = upload_tables(h, s);
+  if (rc) return fail(rc);
+  e = launch_init(h->d_blocks, h->d_geom, (int32_t)P.blocks.size(), h->d_inits, P.dtype, s);
+  if (e != cudaSuccess) return fail(set_error(JACOBI_ECUDA, "init launch failed: %s", cudaGetErrorString(e)));
+  rc = compute_bnorm(h, s);
+  if (rc) return fail(rc);
+  rc = refresh_active(h, s);
+  if (rc) return fail(rc);
+  *out = h;
+  return JACOBI_OK;
+}
+
+int jacobi_create(jacobi_dim3 grid, jacobi_split split, jacobi_dtype dtype, const jacobi_init* init, void* workspace,
+                  size_t ws_bytes, void* stream, jacobi_t** out) {
+  return jacobi_create_batch(1, &grid, &split, dtype, init, workspace, ws_bytes, stream, out);
+}
+
+int jacobi_destroy(jacobi_t* h) {
+  if (!h) return JACOBI_OK;
+  cudaDeviceSynchronize();
+  for (channel_s* c : std::vector<channel_s*>(h->channels)) channel_close(c);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->stage) cudaFree(h->stage);
+  if (h->own_ws && h->ws) cudaFree(h->ws);
+  if (h->h_grids) cudaFreeHost(h->h_grids);
+  if (h->h_norms) cudaFreeHost(h->h_norms);
+  if (h->h_err) cudaFreeHost(h->h_err);
+  delete h;
+  return JACOBI_OK;
+}
+
+int jacobi_info(const jacobi_t* h, jacobi_info_t* out) {
+  if (!h || !out) return set_error(JACOBI_EINVAL, "null argument");
+  out->n_grids = (int64_t)h->plan.grids.size();
+  out->n_blocks = (int64_t)h->plan.blocks.size();
+  out->n_points = h->plan.n_points;
+  out->iteration = h->iter;
+  out->dtype = h->plan.dtype;
+  out->path = h->path;
+  out->halo_bytes_per_iter = h->plan.halo_elems * (int64_t)h->plan.elem;
+  out->workspace_bytes = h->plan.bytes;
+  return JACOBI_OK;
+}
+
+int jacobi_block(const jacobi_t* h, int64_t block, jacobi_block_info* out) {
+  if (!h || !out || block < 0 || block >= (int64_t)h->plan.blocks.size())
+    return set_error(JACOBI_EINVAL, "bad block index");
+  const BlockHost& B = h->plan.blocks[block];
+  out->grid = B.grid;
+  for (int a = 0; a < 3; ++a) {
+    out->origin[a] = B.origin[a];
+    out->extent[a] = B.extent[a];
+  }
+  for (int f = 0; f < 6; ++f) out->neighbour[f] = B.nbr[f];
+  return JACOBI_OK;
+}
+
+int jacobi_set_path(jacobi_t* h, int32_t path) {
+  if (!h || path < JACOBI_PATH_FUSED || path > JACOBI_PATH_GRAPH) return set_error(JACOBI_EINVAL, "bad path");
+  if (h->path != path) h->tables_dirty = true;
+  h->path = path;
+  return JACOBI_OK;
+}
+
+int jacobi_step(jacobi_t* h, int64_t n_iters, void* stream) {
+  if (!h || n_iters < 0) return set_error(JACOBI_EINVAL, "bad arguments to jacobi_step");
+  const cudaStream_t s = S(stream);
+  int rc = do_step(h, n_iters, s);
+  if (rc) return rc;
+  if (h->path == JACOBI_PATH_PERSISTENT) {
+    // The persistent kernel reports expired waits through the error word.
+    cudaError_t q = cudaStreamQuery(s);
+    if (q != cudaSuccess && q != cudaErrorNotReady) return set_error(JACOBI_ECUDA, "%s", cudaGetErrorString(q));
+  }
+  return JACOBI_OK;
+}
+
+int jacobi_residual(jacobi_t* h, double* rel, double* abs_res, void* stream) {
+  if (!h) return set_error(JACOBI_EINVAL, "null handle");
+  const cudaStream_t s = S(stream);
+  int rc = residual_only(h, s);
+  if (rc) return rc;
+  rc = read_norms(h, s);
+  if (rc) return rc;
+  for (size_t g = 0; g < h->plan.grids.size(); ++g) {
+    if (rel) rel[g] = h->h_norms[g].rel;
+    if (abs_res) abs_res[g] = h->h_norms[g].r_norm;
+  }
+  return JACOBI_OK;
+}
+
+int jacobi_solve(jacobi_t* h, double tol, int64_t max_iters, int64_t check_every, int64_t stall_checks,
+                 int64_t* iters_out, double* rel_out, int32_t* status_out, void* stream) {
+  if (!h || check_every < 1 || max_iters < 0 || !(tol >= 0.0))
+    return set_error(JACOBI_EINVAL, "bad arguments to jacobi_solve");
+  const cudaStream_t s = S(stream);
+  Plan& P = h->plan;
+  const size_t ng = P.grids.size();
+  // Every grid starts its solve at its own local iteration 0 of this call.
+  std::vector<int64_t> k(ng, 0), since(ng, 0);
+  std::vector<double> best(ng, INFINITY), rel(ng, 0.0);
+  std::vector<int32_t> status(ng, -1);
+  for (size_t g = 0; g < ng; ++g) activate_grid(h, (int64_t)g);
+  int64_t done_k = 0;  // common local iteration of the active grids
+  for (;;) {
+    const bool check = (done_k % check_every == 0) || done_k == max_iters;
+    int rc;
+    if (check) {
+      if (done_k >= max_iters) {
+        rc = residual_only(h, s);
+      } else {
+        rc = step_with_residual(h, s);
+      }
+      if (rc) return rc;
+      rc = read_norms(h, s);
+      if (rc) return rc;
+      if (h->path == JACOBI_PATH_PERSISTENT) {
+        rc = check_err_word(h, s);
+        if (rc) return rc;
+      }
+      const bool stepped = done_k < max_iters;
+      bool any_active = false;
+      for (size_t g = 0; g < ng; ++g) {
+        GridHost& G = P.grids[g];
+        if (!G.active) continue;
+        const double r = h->h_norms[g].rel;
+        rel[g] = r;
+        k[g] = done_k;
+        int st = -1;
+        if (r <= tol) st = JACOBI_SOLVE_CONVERGED;
+        else if (done_k >= max_iters) st = JACOBI_SOLVE_MAX_ITERS;
+        else if (r < best[g]) { best[g] = r; since[g] = 0; }
+        else if (stall_checks > 0 && ++since[g] >= stall_checks) st = JACOBI_SOLVE_STAGNATED;
+        if (st >= 0) {
+          status[g] = st;
+          // Freeze at u_k: when a step was fused with this check, the grid
+          // already holds u_{k+1} in its other buffer; u_k stays intact.
+          freeze_grid(h, (int64_t)g, grid_local_iter(h, (int64_t)g) - (stepped ? 1 : 0));
+        } else {
+          any_active = true;
+        }
+      }
+      if (!any_active) break;
+      done_k += stepped ? 1 : 0;
+      if (!stepped) break;
+    } else {
+      const int64_t next = std::min<int64_t>((done_k / check_every + 1) * check_every, max_iters);
+      rc = do_step(h, next - done_k, s);
+      if (rc) return rc;
+      done_k = next;
+    }
+  }
+  // Re-activate every grid at its own iteration count.
+  for (size_t g = 0; g < ng; ++g) {
+    activate_grid(h, (int64_t)g);
+    if (iters_out) iters_out[g] = k[g];
+    if (rel_out) rel_out[g] = rel[g];
+    if (status_out) status_out[g] = status[g];
+  }
+  return refresh_active(h, s);
+}
+
+int jacobi_set_state(jacobi_t* h, int64_t grid, const void* src, int32_t src_on_device, void* stream) {
+  if (!h || !src || grid < 0 || grid >= (int64_t)h->plan.grids.size())
+    return set_error(JACOBI_EINVAL, "bad arguments to jacobi_set_state");
+  const cudaStream_t s = S(stream);
+  const GridHost& G = h->plan.grids[grid];
+  const size_t n = (size_t)(G.dims.nx + 2) * (G.dims.ny + 2) * (G.dims.nz + 2) * h->plan.elem;
+  const void* dsrc = src;
+  if (!src_on_device) {
+    void* tmp = nullptr;
+    int rc0 = stage_get(h, n, &tmp);
+    if (rc0) return rc0;
+    JGB_CUDA(cudaMemcpyAsync(tmp, src, n, cudaMemcpyHostToDevice, s));
+    dsrc = tmp;
+  }
+  const int parity = (int)(grid_local_iter(h, grid) & 1);
+  cudaError_t e = launch_scatter(h->d_blocks, h->d_geom, (int32_t)G.block_begin, (int32_t)(G.block_end - G.block_begin),
+                                 dsrc, G.dims.nx, G.dims.ny, G.dims.nz, parity, h->plan.dtype, s);
+  int rc = JACOBI_OK;
+  if (e != cudaSuccess) rc = set_error(JACOBI_ECUDA, "scatter failed: %s", cudaGetErrorString(e));
+  if (!rc) rc = compute_bnorm(h, s);
+  if (!rc && !src_on_device) {
+    // the caller may reuse its host buffer as soon as the call returns
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e2 != cudaSuccess) rc = set_error(JACOBI_ECUDA, "%s", cudaGetErrorString(e2));
+  }
+  return rc;
+}
+
+int jacobi_copy_out(jacobi_t* h, int64_t grid, void* dst, int32_t dst_on_device, int32_t layout, void* stream) {
+  if (!h || !dst || grid < 0 || grid >= (int64_t)h->plan.grids.size() ||
+      (layout != JACOBI_LAYOUT_INTERIOR && layout != JACOBI_LAYOUT_PADDED))
+    return set_error(JACOBI_EINVAL, "bad arguments to jacobi_copy_out");
+  const cudaStream_t s = S(stream);
+  const GridHost& G = h->plan.grids[grid];
+  const int64_t o = layout == JACOBI_LAYOUT_PADDED ? 2 : 0;
+  const size_t n = (size_t)(G.dims.nx + o) * (G.dims.ny + o) * (G.dims.nz + o) * h->plan.elem;
+  void* ddst = dst;
+  void* tmp = nullptr;
+  if (!dst_on_device) {
+    int rc0 = stage_get(h, n, &tmp);
+    if (rc0) return rc0;
+    ddst = tmp;
+  }
+  int rc = JACOBI_OK;
+  cudaError_t e = cudaSuccess;
+  if (layout == JACOBI_LAYOUT_PADDED) e = cudaMemsetAsync(ddst, 0, n, s);
+  const int parity = (int)(grid_local_iter(h, grid) & 1);
+  if (e == cudaSuccess)
+    e = launch_gather(h->d_blocks, h->d_geom, (int32_t)G.block_begin, (int32_t)(G.block_end - G.block_begin), ddst,
+                      G.dims.nx, G.dims.ny, G.dims.nz, parity, layout == JACOBI_LAYOUT_PADDED, h->plan.dtype, s);
+  if (e == cudaSuccess && tmp) e = cudaMemcpyAsync(dst, tmp, n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && tmp) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) rc = set_error(JACOBI_ECUDA, "copy_out failed: %s", cudaGetErrorString(e));
+  return rc;
+}
+
+int jacobi_sync(jacobi_t* h, void* stream) {
+  if (!h) return set_error(JACOBI_EINVAL, "null handle");
+  JGB_CUDA(cudaStreamSynchronize(S(stream)));
+  return check_err_word(h, S(stream));
+}
+
+int jacobi_read_face(jacobi_t* h, int64_t block, int32_t face, void* dst, void* stream) {
+  if (!h || !dst || block < 0 || block >= (int64_t)h->plan.blocks.size() || face < 0 || face > 5)
+    return set_error(JACOBI_EINVAL, "bad arguments to jacobi_read_face");
+  const BlockHost& B = h->plan.blocks[block];
+  const int parity = (int)(grid_local_iter(h, B.grid) & 1);
+  const size_t n = (size_t)face_elems_host(B, face) * h->plan.elem;
+  JGB_CUDA(cudaMemcpyAsync(dst, h->ws + B.recv_off[face][parity], n, cudaMemcpyDeviceToHost, S(stream)));
+  JGB_CUDA(cudaStreamSynchronize(S(stream)));
+  return JACOBI_OK;
+}
+
+int jacobi_debug_drop_block(jacobi_t* h, int64_t block) {
+  if (!h || block < -1 || block >= (int64_t)h->plan.blocks.size()) return set_error(JACOBI_EINVAL, "bad block");
+  h->drop_block = block;
+  h->tables_dirty = true;
+  return JACOBI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,175 @@
+// Device-side definitions shared by the library's kernels: block and work-item
+// tables, rounding-exact arithmetic, the SplitMix64 generator, release/acquire
+// flag operations and bounded waits.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace jgb {
+
+// Faces in the order xm, xp, ym, yp, zm, zp ("m" = low side, "p" = high side).
+enum Face { XM = 0, XP = 1, YM = 2, YP = 3, ZM = 4, ZP = 5 };
+__host__ __device__ inline int opposite(int f) { return f ^ 1; }
+
+// Device error word values (first failure wins).
+enum DevError : uint32_t {
+  DEV_OK = 0,
+  DEV_TIMEOUT = 1,   // a bounded wait expired
+  DEV_SEQ = 2,       // channel sequence / size mismatch
+};
+
+// One block of the decomposition (a "chare" of the paper's Jacobi3D).
+// Interior storage: plane k starts at k * plane_pitch elements, row j of a
+// plane at j * nx; plane_pitch >= nx*ny is rounded up so every plane starts on
+// a 16-byte boundary.  Receive slots, by face, laid out
+//   xm/xp: [k][j] (nz x ny)   ym/yp: [k][i] (nz x nx)   zm/zp: [j][i] (ny x nx)
+// recv[f][p] is read at iterations with parity p; for a Dirichlet face both
+// parities point at the same constant boundary buffer.  send[f][p] is the
+// neighbour's recv[opposite(f)][p] (written with the NEW iterate, at parity
+// p = (it + 1) & 1), or null on a Dirichlet face.
+struct BlockDev {
+  void* u[2];
+  void* recv[6][2];
+  void* send[6][2];
+  int32_t nx, ny, nz;
+  int32_t grid;
+  int64_t plane_pitch;
+  int32_t nbr[6];
+  int32_t pad_[2];
+};
+
+// One CTA's share of a step: block `block`, x-y tile origin (x0, y0) and the
+// z-range [z0, z1).  `slot` indexes the reduction partials.
+struct WorkItem {
+  int32_t block;
+  int32_t slot;
+  int16_t x0, y0;
+  int16_t z0, z1;
+};
+
+// Per-grid state written by the host.
+struct GridDev {
+  int64_t start_iter;   // global iteration at which this grid's local count was 0
+  int32_t item_begin;   // partial slots [item_begin, item_end) belong to this grid
+  int32_t item_end;
+};
+
+// Per-grid norms written by the reduction kernel.
+struct GridNorm {
+  double b_norm2;       // |b|^2, computed once per boundary
+  double r_norm2;       // |b - A u|^2 of the last residual evaluation
+  double r_norm;        // sqrt(r_norm2)
+  double rel;           // r_norm / |b| (r_norm when |b| == 0)
+};
+
+// Tile shape of the table-driven kernels: 32 x 8 threads, each thread walks z.
+constexpr int TX = 32;
+constexpr int TY = 8;
+constexpr int kThreads = TX * TY;
+
+// ---- rounding-exact arithmetic (no contraction into FMA) --------------------
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+
+template <typename T> struct C6;
+template <> struct C6<double> { static constexpr double v = 1.0 / 6.0; };
+template <> struct C6<float> { static constexpr float v = 1.0f / 6.0f; };
+
+// ---- SplitMix64 (Steele, Lea, Flood 2014) as a counter-based generator -------
+// n-th output (0-based) of the stream seeded with `seed`.
+__host__ __device__ inline uint64_t splitmix64(uint64_t seed, uint64_t n) {
+  uint64_t z = seed + (n + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ inline double u01(uint64_t seed, uint64_t n) {
+  return (double)(splitmix64(seed, n) >> 11) * 0x1.0p-53;
+}
+
+// ---- memory-model helpers --------------------------------------------------
+__device__ __forceinline__ int64_t ld_acquire(const int64_t* p) {
+  int64_t v;
+  asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int64_t* p, int64_t v) {
+  asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.volatile.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Spin (bounded by wall time `limit_ns` and by a poll count) until *flag >= target,
+// with acquire semantics.  Returns true on success.  On expiry it records
+// DEV_TIMEOUT in *err (first failure wins); it also gives up early when another
+// waiter has already recorded an error, so one failure stops every waiter.
+__device__ inline bool wait_ge(const int64_t* flag, int64_t target, uint32_t* err,
+                               uint64_t limit_ns) {
+  if (ld_acquire(flag) >= target) return true;
+  const uint64_t t0 = globaltimer_ns();
+  unsigned sleep = 32;
+  for (uint32_t n = 0; n < (1u << 26); ++n) {
+    if (ld_acquire(flag) >= target) return true;
+    if (ld_volatile_u32(err) != DEV_OK) return false;
+    if (globaltimer_ns() - t0 > limit_ns) break;
+    __nanosleep(sleep);
+    if (sleep < 512) sleep <<= 1;
+  }
+  atomicCAS(err, (uint32_t)DEV_OK, (uint32_t)DEV_TIMEOUT);
+  return false;
+}
+
+// Same for 32-bit sequence counters (wrap-safe comparison).
+__device__ inline bool wait_seq_ge(const uint32_t* flag, uint32_t target, uint32_t* err,
+                                   uint64_t limit_ns) {
+  if ((int32_t)(ld_acquire_u32(flag) - target) >= 0) return true;
+  const uint64_t t0 = globaltimer_ns();
+  unsigned sleep = 32;
+  for (uint32_t n = 0; n < (1u << 26); ++n) {
+    if ((int32_t)(ld_acquire_u32(flag) - target) >= 0) return true;
+    if (ld_volatile_u32(err) != DEV_OK) return false;
+    if (globaltimer_ns() - t0 > limit_ns) break;
+    __nanosleep(sleep);
+    if (sleep < 256) sleep <<= 1;
+  }
+  atomicCAS(err, (uint32_t)DEV_OK, (uint32_t)DEV_TIMEOUT);
+  return false;
+}
+
+// Deterministic block-wide FP64 sum (fixed shuffle tree + fixed smem order).
+// All threads of the block must call it; the result is valid in thread 0.
+template <int NT>
+__device__ inline double block_sum(double v, double* smem /* NT/32 doubles */) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31;
+  const int wid = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+  __syncthreads();
+  if (lane == 0) smem[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (wid == 0 && lane == 0) {
+    for (int w = 0; w < NT / 32; ++w) s += smem[w];
+  }
+  return s;
+}
+
+}  // namespace jgb

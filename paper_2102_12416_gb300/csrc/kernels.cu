@@ -1,0 +1,489 @@
+// Jacobi3D kernels for sm_103a: initial state, state scatter/gather, the fused
+// stencil step (stencil + face pack into the neighbours' receive slots +
+// FP64 residual), the explicit pack/copy exchange, the deterministic residual
+// reduction and the persistent kernel whose blocks signal their neighbours
+// through device-side progress flags.
+//
+// The arithmetic follows the Jacobi iteration of the paper's proxy
+// application (Sec. 4.3); the stencil is read as the mean of the six face
+// neighbours, summed as ((xm + xp) + (ym + yp)) + (zm + zp) and multiplied by
+// 1/6 rounded to the state type, every operation rounded on its own.
+#include <cooperative_groups.h>
+
+#include "kernels.cuh"
+
+namespace jgb {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Initial values
+// ---------------------------------------------------------------------------
+__device__ double init_value(const InitDev& I, int64_t gi, int64_t gj, int64_t gk) {
+  const bool bnd = gi == 0 || gj == 0 || gk == 0 || gi == I.NX + 1 || gj == I.NY + 1 ||
+                   gk == I.NZ + 1;
+  const uint64_t idx = ((uint64_t)gk * (uint64_t)(I.NY + 2) + (uint64_t)gj) * (uint64_t)(I.NX + 2) +
+                       (uint64_t)gi;
+  if (!bnd) {
+    if (I.interior == 0) return 0.0;
+    if (I.interior == 1) return u01(I.interior_seed, idx);
+  }
+  if (I.bc == 2) return u01(I.bc_seed, idx);
+  const double x = (double)gi / (double)(I.NX + 1);
+  const double y = (double)gj / (double)(I.NY + 1);
+  const double z = (double)gk / (double)(I.NZ + 1);
+  double g = radd(radd(x, rmul(2.0, y)), rmul(3.0, z));
+  if (I.bc == 1) g = radd(g, rmul(I.noise_amp, u01(I.bc_seed, idx)));
+  return g;
+}
+
+template <typename T> __device__ __forceinline__ T to_state(double v);
+template <> __device__ __forceinline__ double to_state<double>(double v) { return v; }
+template <> __device__ __forceinline__ float to_state<float>(double v) { return __double2float_rn(v); }
+
+// Global padded coordinates of element e of face f of block (B, G).
+__device__ __forceinline__ void face_coords(const BlockDev& B, const BlockGeom& G, int f, int64_t e,
+                                            int64_t& gi, int64_t& gj, int64_t& gk) {
+  const int nx = B.nx, ny = B.ny, nz = B.nz;
+  if (f == XM || f == XP) {
+    const int64_t k = e / ny, j = e % ny;
+    gi = G.ox + (f == XM ? 0 : nx + 1);
+    gj = G.oy + 1 + j;
+    gk = G.oz + 1 + k;
+  } else if (f == YM || f == YP) {
+    const int64_t k = e / nx, i = e % nx;
+    gi = G.ox + 1 + i;
+    gj = G.oy + (f == YM ? 0 : ny + 1);
+    gk = G.oz + 1 + k;
+  } else {
+    const int64_t j = e / nx, i = e % nx;
+    gi = G.ox + 1 + i;
+    gj = G.oy + 1 + j;
+    gk = G.oz + (f == ZM ? 0 : nz + 1);
+  }
+  (void)nz;
+}
+
+__device__ __forceinline__ int64_t face_elems(const BlockDev& B, int f) {
+  if (f == XM || f == XP) return (int64_t)B.nz * B.ny;
+  if (f == YM || f == YP) return (int64_t)B.nz * B.nx;
+  return (int64_t)B.ny * B.nx;
+}
+
+template <typename T>
+__global__ void k_init_interior(const BlockDev* __restrict__ blocks, const BlockGeom* __restrict__ geom,
+                                const InitDev* __restrict__ inits) {
+  const BlockDev& B = blocks[blockIdx.x];
+  const BlockGeom G = geom[blockIdx.x];
+  const InitDev I = inits[G.grid];
+  T* U = (T*)B.u[0];
+  const int64_t nx = B.nx, ny = B.ny, n = nx * ny * B.nz;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    const int64_t i = e % nx, j = (e / nx) % ny, k = e / (nx * ny);
+    U[k * B.plane_pitch + j * nx + i] = to_state<T>(init_value(I, G.ox + 1 + i, G.oy + 1 + j, G.oz + 1 + k));
+  }
+}
+
+template <typename T>
+__global__ void k_init_slots(const BlockDev* __restrict__ blocks, const BlockGeom* __restrict__ geom,
+                             const InitDev* __restrict__ inits) {
+  const BlockDev& B = blocks[blockIdx.x];
+  const BlockGeom G = geom[blockIdx.x];
+  const InitDev I = inits[G.grid];
+  const int f = blockIdx.y;
+  T* S = (T*)B.recv[f][0];
+  const int64_t n = face_elems(B, f);
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    int64_t gi, gj, gk;
+    face_coords(B, G, f, e, gi, gj, gk);
+    S[e] = to_state<T>(init_value(I, gi, gj, gk));
+  }
+}
+
+template <typename T>
+__global__ void k_scatter(const BlockDev* __restrict__ blocks, const BlockGeom* __restrict__ geom, int32_t b0,
+                          const T* __restrict__ src, int64_t NX, int64_t NY, int parity) {
+  const int b = b0 + blockIdx.x;
+  const BlockDev& B = blocks[b];
+  const BlockGeom G = geom[b];
+  const int64_t px = NX + 2, py = NY + 2;
+  if (blockIdx.y == 0) {
+    T* U = (T*)B.u[parity];
+    const int64_t nx = B.nx, ny = B.ny, n = nx * ny * B.nz;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+      const int64_t i = e % nx, j = (e / nx) % ny, k = e / (nx * ny);
+      U[k * B.plane_pitch + j * nx + i] = src[((G.oz + 1 + k) * py + (G.oy + 1 + j)) * px + (G.ox + 1 + i)];
+    }
+  } else {
+    const int f = blockIdx.y - 1;
+    T* S = (T*)B.recv[f][parity];
+    const int64_t n = face_elems(B, f);
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+      int64_t gi, gj, gk;
+      face_coords(B, G, f, e, gi, gj, gk);
+      S[e] = src[(gk * py + gj) * px + gi];
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_gather(const BlockDev* __restrict__ blocks, const BlockGeom* __restrict__ geom, int32_t b0,
+                         T* __restrict__ dst, int64_t NX, int64_t NY, int parity, int padded) {
+  const int b = b0 + blockIdx.x;
+  const BlockDev& B = blocks[b];
+  const BlockGeom G = geom[b];
+  const int64_t off = padded ? 1 : 0;
+  const int64_t px = NX + 2 * off, py = NY + 2 * off;
+  if (blockIdx.y == 0) {
+    const T* U = (const T*)B.u[parity];
+    const int64_t nx = B.nx, ny = B.ny, n = nx * ny * B.nz;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+      const int64_t i = e % nx, j = (e / nx) % ny, k = e / (nx * ny);
+      dst[((G.oz + off + k) * py + (G.oy + off + j)) * px + (G.ox + off + i)] =
+          U[k * B.plane_pitch + j * nx + i];
+    }
+  } else if (padded) {
+    const int f = blockIdx.y - 1;
+    if (B.nbr[f] >= 0) return;  // only Dirichlet faces lie on the padded boundary
+    const T* S = (const T*)B.recv[f][parity];
+    const int64_t n = face_elems(B, f);
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+      int64_t gi, gj, gk;
+      face_coords(B, G, f, e, gi, gj, gk);
+      dst[(gk * py + gj) * px + gi] = S[e];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The stencil sweep of one x-y tile of one block over planes [z0, z1).
+// Thread (tx, ty) owns column (x0 + tx, y0 + ty) and walks z with the planes
+// k-1, k, k+1 of its column in registers.  Neighbours across a block face are
+// read from that face's receive slot (parity p); with kPack the new boundary
+// planes are written into the neighbours' receive slots (parity p ^ 1).
+// Returns this thread's sum of r^2 (FP64) when kResid is set.
+// ---------------------------------------------------------------------------
+template <typename T, int MODE>
+__device__ __forceinline__ double tile_sweep(const BlockDev& B, int p, int x0, int y0, int z0, int z1) {
+  const int i = x0 + threadIdx.x, j = y0 + threadIdx.y;
+  const int nx = B.nx, ny = B.ny, nz = B.nz;
+  double acc = 0.0;
+  if (i >= nx || j >= ny) return acc;
+  const T* __restrict__ U = (const T*)B.u[p];
+  T* __restrict__ V = (T*)B.u[p ^ 1];
+  const int64_t pp = B.plane_pitch;
+  const T* rxm = (const T*)B.recv[XM][p];
+  const T* rxp = (const T*)B.recv[XP][p];
+  const T* rym = (const T*)B.recv[YM][p];
+  const T* ryp = (const T*)B.recv[YP][p];
+  const int64_t col = (int64_t)j * nx + i;
+  T below = (z0 == 0) ? __ldcg((const T*)B.recv[ZM][p] + col) : U[(int64_t)(z0 - 1) * pp + col];
+  T cur = U[(int64_t)z0 * pp + col];
+  const T* rzp = (const T*)B.recv[ZP][p];
+  T* sxm = nullptr; T* sxp = nullptr; T* sym = nullptr; T* syp = nullptr; T* szm = nullptr; T* szp = nullptr;
+  if (MODE & kPack) {
+    if (i == 0) sxm = (T*)B.send[XM][p ^ 1];
+    if (i == nx - 1) sxp = (T*)B.send[XP][p ^ 1];
+    if (j == 0) sym = (T*)B.send[YM][p ^ 1];
+    if (j == ny - 1) syp = (T*)B.send[YP][p ^ 1];
+    szm = (T*)B.send[ZM][p ^ 1];
+    szp = (T*)B.send[ZP][p ^ 1];
+  }
+  for (int k = z0; k < z1; ++k) {
+    const int64_t o = (int64_t)k * pp + col;
+    const T above = (k + 1 < nz) ? U[o + pp] : __ldcg(rzp + col);
+    const T xm = (i > 0) ? U[o - 1] : __ldcg(rxm + (int64_t)k * ny + j);
+    const T xp = (i < nx - 1) ? U[o + 1] : __ldcg(rxp + (int64_t)k * ny + j);
+    const T ym = (j > 0) ? U[o - nx] : __ldcg(rym + (int64_t)k * nx + i);
+    const T yp = (j < ny - 1) ? U[o + nx] : __ldcg(ryp + (int64_t)k * nx + i);
+    const T s = radd(radd(radd(xm, xp), radd(ym, yp)), radd(below, above));
+    if (MODE & kWrite) {
+      const T v = rmul(s, C6<T>::v);
+      V[o] = v;
+      if (MODE & kPack) {
+        if (sxm) sxm[(int64_t)k * ny + j] = v;
+        if (sxp) sxp[(int64_t)k * ny + j] = v;
+        if (sym) sym[(int64_t)k * nx + i] = v;
+        if (syp) syp[(int64_t)k * nx + i] = v;
+        if (k == 0 && szm) szm[col] = v;
+        if (k == nz - 1 && szp) szp[col] = v;
+      }
+    }
+    if (MODE & kResid) {
+      double s64;
+      if (sizeof(T) == 8) {
+        s64 = (double)s;
+      } else {
+        s64 = __dadd_rn(__dadd_rn(__dadd_rn((double)xm, (double)xp), __dadd_rn((double)ym, (double)yp)),
+                        __dadd_rn((double)below, (double)above));
+      }
+      const double r = __dsub_rn(s64, __dmul_rn(6.0, (double)cur));
+      acc = fma(r, r, acc);
+    }
+    below = cur;
+    cur = above;
+  }
+  return acc;
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) k_step(StepLaunch a) {
+  const WorkItem w = a.items[blockIdx.x];
+  const BlockDev& B = a.blocks[w.block];
+  const int p = (int)((a.it - a.grids[B.grid].start_iter) & 1);
+  const double acc = tile_sweep<T, MODE>(B, p, w.x0, w.y0, w.z0, w.z1);
+  if (MODE & kResid) {
+    __shared__ double red[kThreads / 32];
+    const double s = block_sum<kThreads>(acc, red);
+    if (threadIdx.x == 0 && threadIdx.y == 0) a.partials[w.slot] = s;
+  }
+}
+
+// |b|^2 partials: the residual expression with every interior value set to 0,
+// so only Dirichlet ghosts contribute.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_bnorm(StepLaunch a) {
+  const WorkItem w = a.items[blockIdx.x];
+  const BlockDev& B = a.blocks[w.block];
+  const int p = (int)((a.it - a.grids[B.grid].start_iter) & 1);
+  const int i = w.x0 + threadIdx.x, j = w.y0 + threadIdx.y;
+  const int nx = B.nx, ny = B.ny, nz = B.nz;
+  double acc = 0.0;
+  if (i < nx && j < ny) {
+    for (int k = w.z0; k < w.z1; ++k) {
+      double v[6] = {0, 0, 0, 0, 0, 0};
+      if (i == 0 && B.nbr[XM] < 0) v[0] = (double)((const T*)B.recv[XM][p])[(int64_t)k * ny + j];
+      if (i == nx - 1 && B.nbr[XP] < 0) v[1] = (double)((const T*)B.recv[XP][p])[(int64_t)k * ny + j];
+      if (j == 0 && B.nbr[YM] < 0) v[2] = (double)((const T*)B.recv[YM][p])[(int64_t)k * nx + i];
+      if (j == ny - 1 && B.nbr[YP] < 0) v[3] = (double)((const T*)B.recv[YP][p])[(int64_t)k * nx + i];
+      if (k == 0 && B.nbr[ZM] < 0) v[4] = (double)((const T*)B.recv[ZM][p])[(int64_t)j * nx + i];
+      if (k == nz - 1 && B.nbr[ZP] < 0) v[5] = (double)((const T*)B.recv[ZP][p])[(int64_t)j * nx + i];
+      const double sb = __dadd_rn(__dadd_rn(__dadd_rn(v[0], v[1]), __dadd_rn(v[2], v[3])), __dadd_rn(v[4], v[5]));
+      acc = fma(sb, sb, acc);
+    }
+  }
+  __shared__ double red[kThreads / 32];
+  const double s = block_sum<kThreads>(acc, red);
+  if (threadIdx.x == 0 && threadIdx.y == 0) a.partials[w.slot] = s;
+}
+
+// One warp per grid: lane l sums slots item_begin + l, + l + 32, ... in order,
+// then a fixed butterfly combines the lanes.
+__global__ void k_reduce(const GridDev* grids, GridNorm* norms, const int32_t* grid_ids, const double* partials,
+                         int which) {
+  const int g = grid_ids[blockIdx.x];
+  const GridDev G = grids[g];
+  GridNorm& N = norms[g];
+  double s = 0.0;
+  for (int q = G.item_begin + threadIdx.x; q < G.item_end; q += 32) s += partials[q];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) {
+    if (which == 0) {
+      N.r_norm2 = s;
+      N.r_norm = sqrt(s);
+      const double b = sqrt(N.b_norm2);
+      N.rel = b > 0.0 ? N.r_norm / b : N.r_norm;
+    } else {
+      N.b_norm2 = s;
+    }
+  }
+}
+
+// Explicit exchange, step 1: pack each internal face of the new iterate
+// (parity p ^ 1 state) into a contiguous staging buffer.
+template <typename T>
+__global__ void k_pack_faces(const BlockDev* __restrict__ blocks, void* const* staging, const GridDev* grids,
+                             int64_t it) {
+  const int b = blockIdx.x, f = blockIdx.y;
+  const BlockDev& B = blocks[b];
+  if (B.nbr[f] < 0) return;
+  const int p = (int)((it - grids[B.grid].start_iter) & 1);
+  const T* U = (const T*)B.u[p ^ 1];
+  T* S = (T*)staging[b * 6 + f];
+  const int64_t nx = B.nx, ny = B.ny, nz = B.nz, pp = B.plane_pitch;
+  const int64_t n = face_elems(B, f);
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    int64_t i, j, k;
+    if (f == XM || f == XP) { k = e / ny; j = e % ny; i = (f == XM) ? 0 : nx - 1; }
+    else if (f == YM || f == YP) { k = e / nx; i = e % nx; j = (f == YM) ? 0 : ny - 1; }
+    else { j = e / nx; i = e % nx; k = (f == ZM) ? 0 : nz - 1; }
+    S[e] = U[k * pp + j * nx + i];
+  }
+}
+
+// Explicit exchange, step 2: the channel transfer of each packed face into the
+// neighbour's receive slot for the next parity.
+template <typename T>
+__global__ void k_copy_faces(const BlockDev* __restrict__ blocks, void* const* staging, const GridDev* grids,
+                             int64_t it) {
+  const int b = blockIdx.x, f = blockIdx.y;
+  const BlockDev& B = blocks[b];
+  if (B.nbr[f] < 0) return;
+  const int p = (int)((it - grids[B.grid].start_iter) & 1);
+  const T* S = (const T*)staging[b * 6 + f];
+  T* D = (T*)B.send[f][p ^ 1];
+  const int64_t n = face_elems(B, f);
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) D[e] = S[e];
+}
+
+// ---------------------------------------------------------------------------
+// Persistent kernel: CTA c owns active blocks c, c + G, c + 2G, ... for all
+// n_iters iterations.  Before block b computes iteration it (> it0) its CTA
+// acquire-waits until every neighbour's progress flag reaches it (the
+// neighbour finished iteration it - 1, so its faces of u_it are in b's slots
+// and it no longer reads the slots b is about to overwrite); after b's sweep
+// the CTA release-stores progress[b] = it + 1.  Waits are bounded: on expiry
+// the error word is set and every CTA leaves at its next wait.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_persist(PersistLaunch a) {
+  __shared__ double red[kThreads / 32];
+  __shared__ int s_ok;
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  for (int64_t t = 0; t < a.n_iters; ++t) {
+    const int64_t it = a.it0 + t;
+    for (int bi = blockIdx.x; bi < a.n_blocks; bi += gridDim.x) {
+      const int b = a.block_ids[bi];
+      const BlockDev& B = a.blocks[b];
+      if (t > 0) {
+        if (tid == 0) {
+          bool ok = true;
+          for (int f = 0; f < 6 && ok; ++f) {
+            const int nb = B.nbr[f];
+            if (nb >= 0) ok = wait_ge(a.progress + nb, it, a.err, a.wait_ns);
+          }
+          s_ok = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+      }
+      const int p = (int)((it - a.grids[B.grid].start_iter) & 1);
+      const bool resid = a.resid_first && t == 0;
+      for (int q = a.block_items[bi]; q < a.block_items[bi + 1]; ++q) {
+        const WorkItem w = a.items[q];
+        if (resid) {
+          const double acc = tile_sweep<T, kWrite | kPack | kResid>(B, p, w.x0, w.y0, w.z0, w.z1);
+          const double s = block_sum<kThreads>(acc, red);
+          if (tid == 0) a.partials[w.slot] = s;
+        } else {
+          tile_sweep<T, kWrite | kPack>(B, p, w.x0, w.y0, w.z0, w.z1);
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release(a.progress + b, it + 1);
+      }
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_step_t(const StepLaunch& a, int mode, cudaStream_t s) {
+  if (a.n_items <= 0) return cudaSuccess;
+  const dim3 blk(TX, TY);
+  switch (mode) {
+    case kWrite | kPack: k_step<T, kWrite | kPack><<<a.n_items, blk, 0, s>>>(a); break;
+    case kWrite | kPack | kResid: k_step<T, kWrite | kPack | kResid><<<a.n_items, blk, 0, s>>>(a); break;
+    case kWrite: k_step<T, kWrite><<<a.n_items, blk, 0, s>>>(a); break;
+    case kWrite | kResid: k_step<T, kWrite | kResid><<<a.n_items, blk, 0, s>>>(a); break;
+    case kResid: k_step<T, kResid><<<a.n_items, blk, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_step(const StepLaunch& a, int mode, cudaStream_t s) {
+  return a.dtype == 0 ? launch_step_t<double>(a, mode, s) : launch_step_t<float>(a, mode, s);
+}
+
+cudaError_t launch_bnorm(const StepLaunch& a, cudaStream_t s) {
+  if (a.n_items <= 0) return cudaSuccess;
+  const dim3 blk(TX, TY);
+  if (a.dtype == 0) k_bnorm<double><<<a.n_items, blk, 0, s>>>(a);
+  else k_bnorm<float><<<a.n_items, blk, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const GridDev* grids, GridNorm* norms, const int32_t* grid_ids, int32_t n,
+                          const double* partials, int which, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_reduce<<<n, 32, 0, s>>>(grids, norms, grid_ids, partials, which);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_faces(const BlockDev* blocks, int32_t n_blocks, void* const* staging, const GridDev* grids,
+                              int64_t it, int32_t dtype, cudaStream_t s) {
+  if (n_blocks <= 0) return cudaSuccess;
+  const dim3 grid(n_blocks, 6);
+  if (dtype == 0) k_pack_faces<double><<<grid, 256, 0, s>>>(blocks, staging, grids, it);
+  else k_pack_faces<float><<<grid, 256, 0, s>>>(blocks, staging, grids, it);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_faces(const BlockDev* blocks, int32_t n_blocks, void* const* staging, const GridDev* grids,
+                              int64_t it, int32_t dtype, cudaStream_t s) {
+  if (n_blocks <= 0) return cudaSuccess;
+  const dim3 grid(n_blocks, 6);
+  if (dtype == 0) k_copy_faces<double><<<grid, 256, 0, s>>>(blocks, staging, grids, it);
+  else k_copy_faces<float><<<grid, 256, 0, s>>>(blocks, staging, grids, it);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(const BlockDev* blocks, const BlockGeom* geom, int32_t n_blocks, const InitDev* inits,
+                        int32_t dtype, cudaStream_t s) {
+  if (n_blocks <= 0) return cudaSuccess;
+  if (dtype == 0) {
+    k_init_interior<double><<<n_blocks, 256, 0, s>>>(blocks, geom, inits);
+    k_init_slots<double><<<dim3(n_blocks, 6), 256, 0, s>>>(blocks, geom, inits);
+  } else {
+    k_init_interior<float><<<n_blocks, 256, 0, s>>>(blocks, geom, inits);
+    k_init_slots<float><<<dim3(n_blocks, 6), 256, 0, s>>>(blocks, geom, inits);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const BlockDev* blocks, const BlockGeom* geom, int32_t b0, int32_t nb, const void* src,
+                           int64_t NX, int64_t NY, int64_t NZ, int parity, int32_t dtype, cudaStream_t s) {
+  (void)NZ;
+  if (nb <= 0) return cudaSuccess;
+  const dim3 grid(nb, 7);
+  if (dtype == 0) k_scatter<double><<<grid, 256, 0, s>>>(blocks, geom, b0, (const double*)src, NX, NY, parity);
+  else k_scatter<float><<<grid, 256, 0, s>>>(blocks, geom, b0, (const float*)src, NX, NY, parity);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const BlockDev* blocks, const BlockGeom* geom, int32_t b0, int32_t nb, void* dst,
+                          int64_t NX, int64_t NY, int64_t NZ, int parity, int padded, int32_t dtype,
+                          cudaStream_t s) {
+  (void)NZ;
+  if (nb <= 0) return cudaSuccess;
+  const dim3 grid(nb, 7);
+  if (dtype == 0) k_gather<double><<<grid, 256, 0, s>>>(blocks, geom, b0, (double*)dst, NX, NY, parity, padded);
+  else k_gather<float><<<grid, 256, 0, s>>>(blocks, geom, b0, (float*)dst, NX, NY, parity, padded);
+  return cudaGetLastError();
+}
+
+int persistent_max_ctas(int dtype) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  cudaError_t e = dtype == 0
+                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<double>, kThreads, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float>, kThreads, 0);
+  if (e != cudaSuccess) return 0;
+  return per_sm * sms;
+}
+
+cudaError_t launch_persistent(const PersistLaunch& a, int grid_ctas, cudaStream_t s) {
+  if (a.n_blocks <= 0 || a.n_iters <= 0) return cudaSuccess;
+  PersistLaunch args = a;
+  void* params[] = {&args};
+  const dim3 blk(TX, TY);
+  const void* fn = a.dtype == 0 ? (const void*)k_persist<double> : (const void*)k_persist<float>;
+  return cudaLaunchCooperativeKernel(fn, dim3(grid_ctas), blk, params, 0, s);
+}
+
+}  // namespace jgb

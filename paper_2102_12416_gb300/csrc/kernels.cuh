@@ -1,0 +1,87 @@
+// Host-visible launch wrappers for the library's kernels (defined in kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace jgb {
+
+// Initial-state description of one grid, as the init kernels see it.
+struct InitDev {
+  int64_t NX, NY, NZ;  // grid interior size
+  int32_t bc, interior;
+  uint64_t bc_seed, interior_seed;
+  double noise_amp;
+};
+
+// Geometry of one block needed only by init / scatter / gather.
+struct BlockGeom {
+  int32_t ox, oy, oz;  // origin of the first interior point
+  int32_t grid;
+};
+
+struct StepLaunch {
+  const BlockDev* blocks;
+  const WorkItem* items;  // active items
+  int32_t n_items;
+  const GridDev* grids;
+  int64_t it;             // global iteration being computed (u_it -> u_it+1)
+  double* partials;       // per item slot
+  int32_t dtype;          // 0 = f64, 1 = f32
+};
+
+// Step kernels.  mode flags:
+enum StepMode : int { kWrite = 1, kPack = 2, kResid = 4 };
+cudaError_t launch_step(const StepLaunch& a, int mode, cudaStream_t s);
+
+// Explicit exchange: pack every internal face of the NEW iterate into its
+// staging buffer, then copy staging buffers into the neighbours' slots.
+cudaError_t launch_pack_faces(const BlockDev* blocks, int32_t n_blocks, void* const* staging,
+                              const GridDev* grids, int64_t it, int32_t dtype, cudaStream_t s);
+cudaError_t launch_copy_faces(const BlockDev* blocks, int32_t n_blocks, void* const* staging,
+                              const GridDev* grids, int64_t it, int32_t dtype, cudaStream_t s);
+
+// |b|^2 partials (interior = 0, only Dirichlet ghosts).
+cudaError_t launch_bnorm(const StepLaunch& a, cudaStream_t s);
+
+// Sum partials per grid in a fixed order.  which = 0: r_norm2, 1: b_norm2.
+cudaError_t launch_reduce(const GridDev* grids, GridNorm* norms, const int32_t* grid_ids, int32_t n,
+                          const double* partials, int which, cudaStream_t s);
+
+// Initial state: interiors of every block and every receive slot (parity 0
+// for internal faces; the shared buffer for Dirichlet faces).
+cudaError_t launch_init(const BlockDev* blocks, const BlockGeom* geom, int32_t n_blocks,
+                        const InitDev* inits, int32_t dtype, cudaStream_t s);
+
+// Scatter a padded device array of one grid into its blocks (parity p buffers
+// and slots); gather the current iterate back (interior or padded layout).
+cudaError_t launch_scatter(const BlockDev* blocks, const BlockGeom* geom, int32_t b0, int32_t nb,
+                           const void* src, int64_t NX, int64_t NY, int64_t NZ, int parity,
+                           int32_t dtype, cudaStream_t s);
+cudaError_t launch_gather(const BlockDev* blocks, const BlockGeom* geom, int32_t b0, int32_t nb,
+                          void* dst, int64_t NX, int64_t NY, int64_t NZ, int parity, int padded,
+                          int32_t dtype, cudaStream_t s);
+
+// Persistent path: one cooperative launch runs n_iters iterations.
+struct PersistLaunch {
+  const BlockDev* blocks;
+  const WorkItem* items;       // active items, grouped by block
+  const int32_t* block_items;  // per active block: first item index (n_blocks + 1 entries)
+  const int32_t* block_ids;    // active block ids
+  int32_t n_blocks;            // active blocks
+  const GridDev* grids;
+  int64_t it0;
+  int64_t n_iters;
+  int64_t* progress;           // per block: iterations completed (absolute)
+  uint32_t* err;
+  uint64_t wait_ns;
+  double* partials;
+  int32_t resid_first;         // fuse the residual of u_it0 into the first iteration
+  int32_t dtype;
+};
+cudaError_t launch_persistent(const PersistLaunch& a, int grid_ctas, cudaStream_t s);
+int persistent_max_ctas(int dtype);  // co-resident CTA limit (0 on error)
+
+}  // namespace jgb

@@ -1,0 +1,119 @@
+// Host-side runtime structures of the Jacobi3D library (shared by the C-ABI
+// translation units; not part of the public interface).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/jacobi.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace jgb {
+
+// Thread-local message of the last failing call.
+int set_error(int code, const char* fmt, ...);
+#define JGB_CUDA(call)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return ::jgb::set_error(JACOBI_ECUDA, "%s failed: %s (%s:%d)", #call,                 \
+                              cudaGetErrorString(e_), __FILE__, __LINE__);                 \
+  } while (0)
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct BlockHost {
+  int64_t grid;
+  int64_t origin[3], extent[3];
+  int64_t nbr[6];
+  int64_t item_begin, item_end;  // items of this block in the full list
+  int64_t pitch;                 // elements per z-plane
+  size_t u_off[2];
+  size_t recv_off[6][2];
+  size_t stage_off[6];           // explicit-path staging (internal faces only)
+};
+
+struct GridHost {
+  jacobi_dim3 dims;
+  jacobi_split split;
+  jacobi_init init;
+  int64_t counts[3];
+  int64_t block_begin, block_end;
+  int64_t item_begin, item_end;
+  int64_t start_iter;    // global iteration at which the local count was 0
+  int64_t frozen_local;  // local iteration held while inactive
+  bool active;
+};
+
+// Decomposition + workspace layout of a set of grids.
+struct Plan {
+  int32_t dtype;
+  size_t elem;
+  std::vector<GridHost> grids;
+  std::vector<BlockHost> blocks;
+  std::vector<WorkItem> items;
+  int64_t n_points = 0;
+  int64_t halo_elems = 0;  // face elements moved per iteration (internal faces)
+  // byte offsets into the workspace
+  size_t off_blocks, off_geom, off_items, off_active, off_grids, off_norms, off_inits, off_gids, off_partials,
+      off_progress, off_err, off_stage_tab, off_pblock_items, off_pblock_ids;
+  size_t bytes = 0;
+};
+
+int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* splits, jacobi_dtype dtype,
+               const jacobi_init* inits, Plan* out);
+
+}  // namespace jgb
+
+struct channel_s;
+
+struct jacobi_s {
+  jgb::Plan plan;
+  int device = 0;
+  char* ws = nullptr;
+  bool own_ws = false;
+  int32_t path = JACOBI_PATH_FUSED;
+  int64_t iter = 0;  // global iterations completed
+
+  // device tables (inside ws)
+  jgb::BlockDev* d_blocks = nullptr;
+  jgb::BlockGeom* d_geom = nullptr;
+  jgb::WorkItem* d_items = nullptr;
+  jgb::WorkItem* d_active = nullptr;
+  jgb::GridDev* d_grids = nullptr;
+  jgb::GridNorm* d_norms = nullptr;
+  jgb::InitDev* d_inits = nullptr;
+  int32_t* d_gids = nullptr;
+  double* d_partials = nullptr;
+  int64_t* d_progress = nullptr;
+  uint32_t* d_err = nullptr;
+  void** d_stage_tab = nullptr;
+  int32_t* d_pblock_items = nullptr;
+  int32_t* d_pblock_ids = nullptr;
+
+  // host mirrors
+  std::vector<jgb::WorkItem> active_items;
+  std::vector<int32_t> active_blocks;       // block ids of active grids (item-grouped)
+  std::vector<int32_t> active_block_items;  // n_active_blocks + 1 offsets into active_items
+  std::vector<int32_t> active_grids;
+  bool tables_dirty = true;
+  jgb::GridDev* h_grids = nullptr;   // pinned, uploaded to d_grids
+  jgb::GridNorm* h_norms = nullptr;  // pinned, read back from d_norms
+  uint32_t* h_err = nullptr;        // pinned
+
+  // CUDA graph of the fused path
+  cudaGraphExec_t graph = nullptr;
+  int64_t graph_iters = 0;
+  int32_t graph_items = -1;
+
+  uint64_t wait_ns = 1000000000ull;
+  int64_t drop_block = -1;        // fault injection (persistent path)
+  void* stage = nullptr;          // device staging for host transfers
+  size_t stage_bytes = 0;
+  std::vector<channel_s*> channels;
+};

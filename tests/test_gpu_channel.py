@@ -1,0 +1,158 @@
+"""Channel semantics on the GPU (Sec. 3.2.2 Channel API, Sec. 3.1 tag counters).
+
+* payload delivered = payload sent, bit for bit, message by message, in order;
+* zero-copy receives leave message n in the slot of parity n & 1;
+* a size mismatch is reported as JACOBI_ESEQ;
+* a receive with no matching send times out (bounded wait) with
+  JACOBI_ETIMEDOUT instead of hanging, and the context stays usable;
+* the on-device ping-pong completes for 8 B .. 4 MB and leaves the payload.
+"""
+import pytest
+
+import paper_2102_12416_gb300 as jg
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+class _DevBuf:
+    """Raw device bytes viewed as a torch tensor (no copy, no allocation)."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "|u1", "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def _view(ptr, n):
+    return torch.as_tensor(_DevBuf(ptr, n), device="cuda")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2102_12416_gb300 import _build
+    _build.build()
+    jg.load()
+
+
+@pytest.fixture
+def solver(monkeypatch):
+    monkeypatch.setenv("JACOBI_WAIT_MS", "200")
+    s = jg.Jacobi3D((32, 32, 32), ("count", (2, 2, 2)), "f64")
+    yield s
+    s.close()
+
+
+def _payload(n_bytes, tag):
+    g = torch.Generator().manual_seed(1000 + tag)
+    return torch.randint(0, 256, (n_bytes,), dtype=torch.uint8, generator=g).cuda()
+
+
+def test_ordered_exactly_once(solver):
+    ch = jg.channel_open(solver.h, 7, 0, 1, 1 << 16)
+    try:
+        dst = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
+        for k, n in enumerate([16, 4096, 65536, 48, 1024, 8, 12345]):
+            src = _payload(n, k)
+            jg.channel_send(ch, 0, src.data_ptr(), n)
+            jg.channel_recv(ch, 1, dst.data_ptr(), n)
+            jg.channel_sync(ch)
+            assert torch.equal(dst[:n], src), k
+        # both directions interleaved
+        for k in range(6):
+            a, b = _payload(256, 50 + k), _payload(256, 80 + k)
+            jg.channel_send(ch, 0, a.data_ptr(), 256)
+            jg.channel_send(ch, 1, b.data_ptr(), 256)
+            jg.channel_recv(ch, 1, dst.data_ptr(), 256)
+            got_b = dst[:256].clone()
+            jg.channel_recv(ch, 0, dst.data_ptr(), 256)
+            jg.channel_sync(ch)
+            assert torch.equal(got_b, a) and torch.equal(dst[:256], b)
+    finally:
+        jg.channel_close(ch)
+
+
+def test_two_in_flight_then_receive(solver):
+    ch = jg.channel_open(solver.h, 8, 2, 3, 4096)
+    try:
+        m0, m1 = _payload(4096, 1), _payload(4096, 2)
+        jg.channel_send(ch, 2, m0.data_ptr(), 4096)
+        jg.channel_send(ch, 2, m1.data_ptr(), 4096)
+        d0 = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+        d1 = torch.zeros_like(d0)
+        jg.channel_recv(ch, 3, d0.data_ptr(), 4096)
+        jg.channel_recv(ch, 3, d1.data_ptr(), 4096)
+        jg.channel_sync(ch)
+        assert torch.equal(d0, m0) and torch.equal(d1, m1)
+    finally:
+        jg.channel_close(ch)
+
+
+def test_zero_copy_slot(solver):
+    ch = jg.channel_open(solver.h, 9, 0, 4, 1024)
+    try:
+        for n in range(4):
+            m = _payload(1024, 10 + n)
+            jg.channel_send(ch, 0, m.data_ptr(), 1024)
+            jg.channel_recv(ch, 4, None, 1024)
+            jg.channel_sync(ch)
+            slot = _view(jg.channel_slot(ch, 4, n & 1), 1024)
+            assert torch.equal(slot, m), n
+    finally:
+        jg.channel_close(ch)
+
+
+def test_size_mismatch_is_seq_error(solver):
+    ch = jg.channel_open(solver.h, 10, 5, 6, 1024)
+    try:
+        m = _payload(512, 3)
+        d = torch.zeros(1024, dtype=torch.uint8, device="cuda")
+        jg.channel_send(ch, 5, m.data_ptr(), 512)
+        jg.channel_recv(ch, 6, d.data_ptr(), 1024)
+        with pytest.raises(jg.JacobiError) as e:
+            jg.channel_sync(ch)
+        assert e.value.code == jg.JACOBI_ESEQ
+    finally:
+        jg.channel_close(ch)
+
+
+def test_recv_without_send_times_out(solver):
+    ch = jg.channel_open(solver.h, 11, 0, 7, 256)
+    try:
+        d = torch.zeros(256, dtype=torch.uint8, device="cuda")
+        jg.channel_recv(ch, 7, d.data_ptr(), 256)  # nothing was sent
+        with pytest.raises(jg.JacobiError) as e:
+            jg.channel_sync(ch)
+        assert e.value.code == jg.JACOBI_ETIMEDOUT
+    finally:
+        jg.channel_close(ch)
+    # the GPU context is still usable afterwards
+    solver.step(2)
+    solver.sync()
+
+
+def test_duplicate_channel_id_rejected(solver):
+    ch = jg.channel_open(solver.h, 12, 0, 1, 64)
+    try:
+        with pytest.raises(jg.JacobiError) as e:
+            jg.channel_open(solver.h, 12, 2, 3, 64)
+        assert e.value.code == jg.JACOBI_EINVAL
+    finally:
+        jg.channel_close(ch)
+
+
+@pytest.mark.parametrize("nbytes,ctas", [(8, 1), (4096, 1), (65536, 2), (1 << 20, 16), (4 << 20, 32)])
+def test_pingpong_runs_and_delivers(solver, nbytes, ctas):
+    ch = jg.channel_open(solver.h, 20, 0, 1, 4 << 20)
+    try:
+        # the ping-pong sends each endpoint's parity-1 slot into the peer's parity-0 slot
+        a, b = _payload(nbytes, 1), _payload(nbytes, 2)
+        _view(jg.channel_slot(ch, 0, 1), nbytes).copy_(a)
+        _view(jg.channel_slot(ch, 1, 1), nbytes).copy_(b)
+        torch.cuda.synchronize()
+        jg.channel_pingpong(ch, nbytes, 10, ctas)
+        jg.channel_sync(ch)
+        assert torch.equal(_view(jg.channel_slot(ch, 1, 0), nbytes), a)
+        assert torch.equal(_view(jg.channel_slot(ch, 0, 0), nbytes), b)
+    finally:
+        jg.channel_close(ch)

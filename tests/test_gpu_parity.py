@@ -1,0 +1,280 @@
+"""GPU parity of the CUDA path against the CPU oracle, through the C ABI.
+
+Bars (stated here, derived in the design doc):
+  * init, pack/unpack, decomposition and the FP64 stencil: bit-exact;
+  * FP32 stencil: bit-exact against the FP32 oracle (same operation order),
+    and within 1e-5 relative (inf-norm) of the FP64 oracle after the stated
+    iterations;
+  * residual norms: within 1e-12 relative (the summation order differs);
+  * solve iteration counts: equal.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import jacobi_inputs as J
+import paper_2102_12416_gb300 as jg
+
+pytestmark = pytest.mark.gpu
+
+RES_TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2102_12416_gb300 import _build
+    _build.build()
+    jg.load()
+
+
+def _mask_edges(p):
+    """Padded copy_out writes edges and corners as 0 (the stencil never reads them)."""
+    q = p.copy()
+    nz, ny, nx = q.shape
+    for a in (0, -1):
+        for b in (0, -1):
+            q[a, b, :] = 0
+            q[a, :, b] = 0
+            q[:, a, b] = 0
+    return q
+
+
+def _solver(grid, split, dtype="f64", init=None, path="fused"):
+    return jg.Jacobi3D(grid, split, dtype, init, path=path)
+
+
+INIT_CASES = [
+    ((64, 64, 64), ("count", (2, 2, 2)), "f64", dict(bc="linear", interior="uniform", interior_seed=0)),
+    ((45, 37, 29), ("count", (3, 5, 7)), "f64", dict(bc="uniform", bc_seed=1, interior="zero")),
+    ((50, 20, 33), ("shape", (16, 16, 16)), "f32", dict(bc="linear_noise", bc_seed=3, noise_amp=1e-3)),
+    ((33, 47, 18), ("shape", (32, 32, 32)), "f32", dict(bc="uniform", bc_seed=9, interior="uniform",
+                                                        interior_seed=10)),
+]
+
+
+@pytest.mark.parametrize("grid,split,dtype,init", INIT_CASES)
+def test_init_matches_shared_generator(grid, split, dtype, init):
+    with _solver(grid, split, dtype, init) as s:
+        got = s.copy_out(padded=True)
+    want = J.initial_grid(*grid, dtype=np.float64 if dtype == "f64" else np.float32, **init)
+    assert np.array_equal(got, _mask_edges(want))
+
+
+def test_set_state_roundtrip():
+    grid = (40, 31, 22)
+    u = J.initial_grid(*grid, "uniform", bc_seed=5, interior="uniform", interior_seed=6)
+    with _solver(grid, ("shape", (16, 8, 8))) as s:
+        s.set_state(u)
+        assert np.array_equal(s.copy_out(padded=True), _mask_edges(u))
+        assert np.array_equal(s.copy_out(), J.interior_of(u))
+
+
+@pytest.mark.parametrize("path", ["fused", "explicit", "persistent", "graph"])
+def test_config1_bit_exact(oracle_mod, path):
+    """64^3 FP64, 2x2x2 blocks of 32^3, linear boundary, U[0,1) interior, 100 iterations."""
+    w = J.WORKLOADS["jacobi3d-fp64-64c-2x2x2"]
+    init = dict(bc=w["bc"], bc_seed=w["bc_seed"], interior=w["interior"], interior_seed=w["interior_seed"])
+    u0 = J.initial_grid(*w["grid"], **init)
+    want = oracle_mod.jacobi(u0, w["iters"])
+    with _solver(w["grid"], w["split"], "f64", init, path) as s:
+        s.step(w["iters"])
+        s.sync()
+        got = s.copy_out(padded=True)
+    assert np.array_equal(got, _mask_edges(want))
+
+
+SPLITS = [("count", (1, 1, 1)), ("count", (2, 2, 2)), ("count", (3, 5, 7)), ("shape", (16, 16, 16)),
+          ("shape", (7, 9, 5)), ("shape", (45, 8, 29))]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("path", ["fused", "persistent"])
+def test_decomposition_invariance(oracle_mod, dtype, path):
+    grid = (45, 37, 29)
+    init = dict(bc="uniform", bc_seed=21, interior="uniform", interior_seed=22)
+    npdt = np.float64 if dtype == "f64" else np.float32
+    u0 = J.initial_grid(*grid, dtype=npdt, **init)
+    want = oracle_mod.jacobi(u0, 13)
+    for split in SPLITS:
+        with _solver(grid, split, dtype, init, path) as s:
+            s.step(13)
+            got = s.copy_out()
+        assert np.array_equal(got, J.interior_of(want)), (split, path)
+
+
+def test_fp32_error_vs_fp64_oracle(oracle_mod):
+    grid = (64, 64, 64)
+    init = dict(bc="linear_noise", bc_seed=3, noise_amp=1e-3, interior="zero")
+    ref = oracle_mod.jacobi(J.initial_grid(*grid, **init), 200)
+    with _solver(grid, ("count", (2, 2, 2)), "f32", init) as s:
+        s.step(200)
+        got = s.copy_out().astype(np.float64)
+    err = np.max(np.abs(got - J.interior_of(ref))) / np.max(np.abs(J.interior_of(ref)))
+    assert err <= 1e-5
+
+
+def test_packed_faces_equal_neighbour_planes():
+    """After k steps every receive slot holds the neighbour's boundary plane of
+    u_k (pack + channel transfer, fused or explicit) or the Dirichlet values."""
+    grid = (40, 24, 19)
+    init = dict(bc="uniform", bc_seed=31, interior="uniform", interior_seed=32)
+    for path in ("fused", "explicit"):
+        with _solver(grid, ("shape", (16, 8, 8)), "f64", init, path) as s:
+            s.step(3)
+            full = s.copy_out(padded=True)
+            full_ref = J.initial_grid(*grid, **init)
+            for b in range(s.info.n_blocks):
+                bi = s.block(b)
+                (ox, oy, oz), (ex, ey, ez) = tuple(bi.origin), tuple(bi.extent)
+                # ghost planes around the block, from the gathered padded grid
+                # (boundary values come from the generator: padded copy_out of a
+                # Dirichlet face is itself the slot, so use the generator there)
+                src = full.copy()
+                src[0], src[-1] = full_ref[0], full_ref[-1]
+                src[:, 0], src[:, -1] = full_ref[:, 0], full_ref[:, -1]
+                src[:, :, 0], src[:, :, -1] = full_ref[:, :, 0], full_ref[:, :, -1]
+                zs, ys, xs = slice(oz + 1, oz + 1 + ez), slice(oy + 1, oy + 1 + ey), slice(ox + 1, ox + 1 + ex)
+                want = {
+                    0: src[zs, ys, ox], 1: src[zs, ys, ox + ex + 1],
+                    2: src[zs, oy, xs], 3: src[zs, oy + ey + 1, xs],
+                    4: src[oz, ys, xs], 5: src[oz + ez + 1, ys, xs],
+                }
+                for f in range(6):
+                    assert np.array_equal(s.read_face(b, f), want[f]), (path, b, f)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_residual_parity(oracle_mod, dtype):
+    grid = (37, 29, 41)
+    init = dict(bc="linear_noise", bc_seed=7, noise_amp=1e-3, interior="uniform", interior_seed=8)
+    npdt = np.float64 if dtype == "f64" else np.float32
+    u0 = J.initial_grid(*grid, dtype=npdt, **init)
+    for k in (0, 9):
+        uk = oracle_mod.jacobi(u0, k)
+        rn, bn, rel = oracle_mod.residual(uk)
+        with _solver(grid, ("shape", (16, 16, 16)), dtype, init) as s:
+            s.step(k)
+            grel, gabs = s.residual()
+        assert abs(gabs[0] - rn) <= RES_TOL * rn
+        assert abs(grel[0] - rel) <= RES_TOL * rel
+
+
+def test_residual_closed_form_linear():
+    """At the linear fixed point the residual is rounding noise."""
+    grid = (48, 40, 36)
+    with _solver(grid, ("count", (2, 2, 2)), "f64", dict(bc="linear", interior="bc")) as s:
+        rel, _ = s.residual()
+    assert rel[0] <= 1e-15
+
+
+@pytest.mark.parametrize("path", ["fused", "persistent"])
+def test_solve_matches_oracle(oracle_mod, path):
+    grid = (20, 16, 12)
+    init = dict(bc="uniform", bc_seed=41, interior="zero")
+    u0 = J.initial_grid(*grid, **init)
+    tol, cap, check = 1e-8, 5000, 7
+    want, k, rel, st = oracle_mod.solve(u0, tol, cap, check)
+    with _solver(grid, ("shape", (8, 8, 8)), "f64", init, path) as s:
+        it, grel, gst = s.solve(tol, cap, check)
+        got = s.copy_out(padded=True)
+    assert (it[0], gst[0]) == (k, st)
+    assert abs(grel[0] - rel) <= RES_TOL * rel
+    assert np.array_equal(got, _mask_edges(want))
+
+
+def test_solve_cap_and_stagnation(oracle_mod):
+    grid = (16, 16, 16)
+    init = dict(bc="linear_noise", bc_seed=3, noise_amp=1e-3, interior="zero")
+    with _solver(grid, ("count", (2, 2, 2)), "f32", init) as s:
+        it, rel, st = s.solve(1e-14, 100000, 10, stall_checks=5)
+    u0 = J.initial_grid(*grid, dtype=np.float32, **init)
+    _, k, orel, ost = oracle_mod.solve(u0, 1e-14, 100000, 10, stall_checks=5)
+    assert st[0] == jg.JACOBI_SOLVE_STAGNATED == ost and it[0] == k
+    with _solver(grid, ("count", (2, 2, 2)), "f64", init) as s:
+        it, rel, st = s.solve(1e-30, 23, 10)
+    assert (it[0], st[0]) == (23, jg.JACOBI_SOLVE_MAX_ITERS)
+
+
+def test_batched_solve_alone_equals_mix(oracle_mod):
+    """Each grid's result in a batch is bit-identical to solving it alone."""
+    grids = [(24, 16, 40), (16, 16, 16), (48, 32, 16)]
+    inits = [dict(bc="uniform", bc_seed=(2 << 32) | g, interior="zero") for g in range(3)]
+    splits = [("shape", (16, 16, 16))] * 3
+    with jg.Jacobi3D(grids, splits, "f64", inits) as s:
+        its, rels, sts = s.solve(1e-7, 20000, 10)
+        mix = [s.copy_out(g) for g in range(3)]
+    for g in range(3):
+        with jg.Jacobi3D([grids[g]], [splits[g]], "f64", [inits[g]]) as s1:
+            it1, rel1, st1 = s1.solve(1e-7, 20000, 10)
+            alone = s1.copy_out()
+        assert (it1[0], st1[0], rel1[0]) == (its[g], sts[g], rels[g])
+        assert np.array_equal(alone, mix[g])
+        _, k, _, _ = oracle_mod.solve(J.initial_grid(*grids[g], **inits[g]), 1e-7, 20000, 10)
+        assert k == its[g]
+
+
+# ---- the 512^3 FP64 workload (8x8x8 blocks of 64^3) -------------------------------
+
+def _cfg2():
+    w = J.WORKLOADS["jacobi3d-fp64-512c-8x8x8"]
+    init = dict(bc=w["bc"], bc_seed=w["bc_seed"], interior=w["interior"], interior_seed=w["interior_seed"])
+    return w, init
+
+
+def test_config2_full_size_vs_oracle(oracle_mod):
+    """Full 512^3 grid, the benchmark's launch configuration, 260 iterations (the
+    front from the boundary has reached every point), compared bit for bit."""
+    w, init = _cfg2()
+    u0 = J.initial_grid(*w["grid"], **init)
+    want = oracle_mod.jacobi(u0, 260)
+    with _solver(w["grid"], w["split"], "f64", init, "graph") as s:
+        s.step(260)
+        got = s.copy_out()
+    assert np.array_equal(got, J.interior_of(want))
+
+
+def test_config2_invariance_1000_iters():
+    """1000 iterations: 8x8x8 blocks equal 2x2x2 blocks bit for bit."""
+    w, init = _cfg2()
+    outs = []
+    for split in (w["split"], ("count", (2, 2, 2))):
+        with _solver(w["grid"], split, "f64", init, "graph") as s:
+            s.step(w["iters"])
+            outs.append(s.copy_out())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_config2_eigenmode_closed_form():
+    """Eigenmode decay after 1000 iterations at full size: lambda^1000 exactly."""
+    w, _ = _cfg2()
+    nx, ny, nz = w["grid"]
+    g = J.initial_grid(nx, ny, nz, "linear", interior="bc")
+    x, y, z = J.coordinates(nx, ny, nz)
+    mode = np.sin(np.pi * z)[:, None, None] * np.sin(np.pi * y)[None, :, None] * np.sin(2 * np.pi * x)[None, None, :]
+    u0 = g.copy()
+    J.interior_of(u0)[...] += 0.5 * J.interior_of(mode)
+    lam = (math.cos(2 * math.pi / (nx + 1)) + math.cos(math.pi / (ny + 1)) + math.cos(math.pi / (nz + 1))) / 3
+    with _solver(w["grid"], w["split"], "f64", dict(bc="linear", interior="bc"), "graph") as s:
+        s.set_state(u0)
+        s.step(w["iters"])
+        got = s.copy_out() - J.interior_of(g)
+    want = lam ** w["iters"] * 0.5 * J.interior_of(mode)
+    assert np.max(np.abs(got - want)) <= 1e-11 * np.max(np.abs(want))
+
+
+# ---- failure detection: bounded waits, no hang ----------------------------------
+
+def test_persistent_wait_times_out(monkeypatch):
+    monkeypatch.setenv("JACOBI_WAIT_MS", "200")
+    with _solver((32, 32, 32), ("count", (2, 2, 2)), "f64", None, "persistent") as s:
+        jg.jacobi_debug_drop_block(s.h, 3)
+        s.step(5)
+        with pytest.raises(jg.JacobiError) as e:
+            s.sync()
+        assert e.value.code == jg.JACOBI_ETIMEDOUT
+        jg.jacobi_debug_drop_block(s.h, -1)
+    # the context is still usable
+    with _solver((32, 32, 32), ("count", (2, 2, 2)), "f64", None, "persistent") as s:
+        s.step(3)
+        s.sync()

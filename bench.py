@@ -46,6 +46,7 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default=DEFAULT_WORKLOAD)
     p.add_argument("--path", default="graph", choices=["fused", "graph", "persistent", "explicit"])
+    p.add_argument("--iters", type=int, default=0, help="override the workload's iterations per step")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--cpu-iters", type=int, default=4, help="oracle iterations in the CPU sample")
     p.add_argument("--no-sweep", action="store_true", help="skip the channel ping-pong sweep")
@@ -182,7 +183,9 @@ def run_reference(args):
     if rank != 0:
         return 0
     import jacobi_inputs as J
-    w = J.WORKLOADS[args.workload]
+    w = dict(J.WORKLOADS[args.workload])
+    if args.iters > 0:
+        w["iters"] = args.iters
     for _ in range(args.warmup):
         cpu_baseline(w, args.cpu_iters)
     vals, secs = [], []
@@ -247,7 +250,9 @@ def run_ours(args):
         dist.barrier()
     jg.load()
 
-    w = J.WORKLOADS[args.workload]
+    w = dict(J.WORKLOADS[args.workload])
+    if args.iters > 0:
+        w["iters"] = args.iters
     iters = w["iters"]
     init = dict(bc=w["bc"], bc_seed=w["bc_seed"], interior=w["interior"], interior_seed=w["interior_seed"])
     if "noise_amp" in w:
@@ -324,7 +329,8 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    for _ in range(args.e2e_steps):
+    e2e_steps = max(args.e2e_steps, 1)
+    for _ in range(e2e_steps):
         jg.jacobi_set_state(s.h, 0, h_in.data_ptr(), False, stream)
         s.step(iters)
         s.residual()
@@ -336,9 +342,9 @@ def run_ours(args):
         t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
-    e2e = {"value": world * n_points * iters * args.e2e_steps / (e2e_ms * 1e-3) / 1e9, "unit": "GLUP/s",
+    e2e = {"value": world * n_points * iters * e2e_steps / (e2e_ms * 1e-3) / 1e9, "unit": "GLUP/s",
            "h2d_bytes_per_step": h_in.numel() * h_in.element_size(),
-           "d2h_bytes_per_step": h_out.numel() * h_out.element_size() + 8 * 4, "steps": args.e2e_steps}
+           "d2h_bytes_per_step": h_out.numel() * h_out.element_size() + 8 * 4, "steps": e2e_steps}
 
     sweep = None
     if not args.no_sweep and rank == 0:

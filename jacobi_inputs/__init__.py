@@ -133,9 +133,17 @@ WORKLOADS = {
     "jacobi3d-fp64-512c-8x8x8": dict(grid=(512, 512, 512), split=("count", (8, 8, 8)), dtype="f64",
                                      bc="uniform", bc_seed=1, interior="zero", interior_seed=0,
                                      iters=1000),
+    # 256^3 versions of the two above: small cases for profiler captures
+    # (two 134 MB FP64 state copies, still larger than L2).
+    "jacobi3d-fp64-256c-4x4x4": dict(grid=(256, 256, 256), split=("count", (4, 4, 4)), dtype="f64",
+                                     bc="uniform", bc_seed=1, interior="zero", interior_seed=0,
+                                     iters=20),
+    "jacobi3d-fp32-256c-4x4x4": dict(grid=(256, 256, 256), split=("count", (4, 4, 4)), dtype="f32",
+                                     bc="linear_noise", bc_seed=3, noise_amp=1e-3,
+                                     interior="zero", interior_seed=0, iters=20),
     "jacobi3d-fp32-768c-12x12x12": dict(grid=(768, 768, 768), split=("count", (12, 12, 12)),
                                         dtype="f32", bc="linear_noise", bc_seed=3, noise_amp=1e-3,
-                                        interior="zero", interior_seed=0, tol=1e-6),
+                                        interior="zero", interior_seed=0, tol=1e-6, iters=200),
 }
 
 

@@ -256,6 +256,34 @@ int jacobi_read_face(jacobi_t* h, int64_t block, int32_t face, void* dst, void* 
  * clears the injection. */
 int jacobi_debug_drop_block(jacobi_t* h, int64_t block);
 
+/* ---- allocation-free residual ------------------------------------------------- */
+
+/* Largest nz accepted by jacobi_residual_noalloc (size of its fixed scratch). */
+#define JACOBI_NOALLOC_MAX_PLANES 16384
+
+/* The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory when they need a residual: code running while a
+ * stream is being captured into a CUDA graph (an allocation there is not a
+ * stream operation and breaks or is refused by the capture), and applications
+ * that reserve all device memory at start-up and forbid later allocations.
+ *
+ * Computes the FP64 residual of a caller-owned padded state array u_padded
+ * (device memory, (nz+2)*(ny+2)*(nx+2) values of `dtype`, x fastest, boundary
+ * included) with the same per-point expression as jacobi_residual, and writes
+ * out[0] = |b - Au|, out[1] = |b|, out[2] = rel (|b| = 0: rel = |b - Au|) to
+ * the caller's device buffer `out` (3 doubles), asynchronously on `stream`.
+ * It allocates nothing and calls no allocating routine: the reduction scratch
+ * is a fixed 256 KB device array inside the library (two FP64 partials per
+ * z-plane), held by every GPU that loads the library until the process exits.
+ * Grids with nz > JACOBI_NOALLOC_MAX_PLANES are rejected with JACOBI_EINVAL.
+ * The first call on each device looks up the array's device address (no
+ * allocation, but it may load the module), so make that first call before
+ * any stream capture.  All calls on a device share the array and each call
+ * overwrites every partial it reads; calls whose kernels overlap on the GPU
+ * (unordered streams) race on it. */
+int jacobi_residual_noalloc(const void* u_padded, jacobi_dim3 grid, jacobi_dtype dtype, double* out,
+                            void* stream);
+
 /* ---- channels (Sec. 3.1 tag scheme, Sec. 3.2.2 Channel API) ------------------ */
 
 /* Open a two-sided channel between blocks a and b with a caller-chosen id

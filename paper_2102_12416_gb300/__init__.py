@@ -96,6 +96,7 @@ _SIGS = {
     "jacobi_sync": (ctypes.c_int, [P, P]),
     "jacobi_read_face": (ctypes.c_int, [P, c_int64, c_int32, P, P]),
     "jacobi_debug_drop_block": (ctypes.c_int, [P, c_int64]),
+    "jacobi_residual_noalloc": (ctypes.c_int, [P, jacobi_dim3, ctypes.c_int, P, P]),
     "channel_open": (ctypes.c_int, [P, c_uint32, c_int64, c_int64, c_size_t, ctypes.POINTER(P)]),
     "channel_send": (ctypes.c_int, [P, c_int64, P, c_size_t, P]),
     "channel_recv": (ctypes.c_int, [P, c_int64, P, c_size_t, P]),
@@ -274,6 +275,16 @@ def jacobi_read_face(h, block, face, dst: np.ndarray, stream=None):
 
 def jacobi_debug_drop_block(h, block):
     _call("jacobi_debug_drop_block", h, block)
+
+
+JACOBI_NOALLOC_MAX_PLANES = 16384
+
+
+def jacobi_residual_noalloc(u_padded_dev, grid, dtype, out_dev, stream=None):
+    """Residual of a device padded array into a device buffer of 3 doubles
+    (|r|, |b|, rel); allocates nothing (see include/jacobi.h)."""
+    _call("jacobi_residual_noalloc", int(u_padded_dev), jacobi_dim3(*grid), DTYPES[dtype], int(out_dev),
+          _stream(stream))
 
 
 def channel_open(h, channel_id, block_a, block_b, max_bytes) -> int:

@@ -49,6 +49,25 @@ static int axis_split(int64_t n, int32_t mode, int64_t param, std::vector<std::p
   return JACOBI_OK;
 }
 
+// Rows per thread for the plane-streaming path, or 0 when the block shape does
+// not fit it: rows must split into 16-byte vectors (which also keeps every
+// bulk copy 16-byte aligned), one CTA of kThreads threads must cover a plane
+// with at most 8 rows per thread, and a ring stage must fit shared memory.
+static int stream_rows(int64_t nx, int64_t ny, size_t elem, uint32_t* stage_bytes) {
+  const int64_t vec = 16 / (int64_t)elem;
+  if (nx % vec || ny % vec) return 0;
+  const int64_t txv = nx / vec;
+  if (txv > kThreads) return 0;
+  const uint64_t stage = ((uint64_t)(nx * ny + 2 * (nx + ny)) * elem + 127) / 128 * 128;
+  if (128 + 4 * stage > (uint64_t)kMaxStepSmem) return 0;
+  for (int ry = 1; ry <= 8; ry *= 2)
+    if (ny % ry == 0 && txv * (ny / ry) <= kThreads) {
+      *stage_bytes = (uint32_t)stage;
+      return ry;
+    }
+  return 0;
+}
+
 static int64_t face_elems_host(const BlockHost& b, int f) {
   if (f < 2) return b.extent[1] * b.extent[2];
   if (f < 4) return b.extent[0] * b.extent[2];
@@ -114,33 +133,48 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
         }
     G.block_end = (int64_t)P->blocks.size();
     if (G.block_end > (1ll << 30)) return set_error(JACOBI_EINVAL, "too many blocks");
-    // Work items of this grid: tiles of TX x TY columns; the z-chunk depends
-    // only on this grid, so a grid's items (and its residual summation order)
-    // are the same alone or in a batch.
-    int64_t tiles = 0, maxz = 0;
+    // Work items of this grid.  Blocks that fit the plane-streaming path get
+    // one item per z-chunk; the others one item per TX x TY tile and z-chunk.
+    // The chunk depends only on this grid, so a grid's items (and its
+    // residual summation order) are the same alone or in a batch.
+    int64_t units = 0, maxz = 0;
+    std::vector<int> rows(G.block_end - G.block_begin);
     for (int64_t b = G.block_begin; b < G.block_end; ++b) {
       const BlockHost& B = P->blocks[b];
-      tiles += ((B.extent[0] + TX - 1) / TX) * ((B.extent[1] + TY - 1) / TY);
+      uint32_t sb = 0;
+      const int ry = stream_rows(B.extent[0], B.extent[1], P->elem, &sb);
+      rows[b - G.block_begin] = ry;
+      if (ry) P->max_stage = std::max(P->max_stage, sb);
+      units += ry ? 1 : ((B.extent[0] + TX - 1) / TX) * ((B.extent[1] + TY - 1) / TY);
       maxz = std::max(maxz, B.extent[2]);
     }
     int64_t zc = maxz;
-    while (zc > 8 && tiles * ((maxz + zc - 1) / zc) < 1024) zc = (zc + 1) / 2;
+    while (zc > 16 && units * ((maxz + zc - 1) / zc) < 2048) zc = (zc + 1) / 2;
     G.item_begin = (int64_t)P->items.size();
     for (int64_t b = G.block_begin; b < G.block_end; ++b) {
       BlockHost& B = P->blocks[b];
+      const int ry = rows[b - G.block_begin];
       B.item_begin = (int64_t)P->items.size();
-      for (int64_t z0 = 0; z0 < B.extent[2]; z0 += zc)
+      for (int64_t z0 = 0; z0 < B.extent[2]; z0 += zc) {
+        WorkItem w;
+        w.block = (int32_t)b;
+        w.z0 = (int16_t)z0;
+        w.z1 = (int16_t)std::min(B.extent[2], z0 + zc);
+        if (ry) {
+          w.slot = (int32_t)P->items.size();
+          w.x0 = -1;
+          w.y0 = (int16_t)ry;
+          P->items.push_back(w);
+          continue;
+        }
         for (int64_t y0 = 0; y0 < B.extent[1]; y0 += TY)
           for (int64_t x0 = 0; x0 < B.extent[0]; x0 += TX) {
-            WorkItem w;
-            w.block = (int32_t)b;
             w.slot = (int32_t)P->items.size();
             w.x0 = (int16_t)x0;
             w.y0 = (int16_t)y0;
-            w.z0 = (int16_t)z0;
-            w.z1 = (int16_t)std::min(B.extent[2], z0 + zc);
             P->items.push_back(w);
           }
+      }
       B.item_end = (int64_t)P->items.size();
     }
     G.item_end = (int64_t)P->items.size();
@@ -155,6 +189,7 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
   P->off_geom = take(nb * sizeof(BlockGeom));
   P->off_items = take(ni * sizeof(WorkItem));
   P->off_active = take(ni * sizeof(WorkItem));
+  P->off_kind = take(ni * sizeof(WorkItem));
   P->off_grids = take(ng * sizeof(GridDev));
   P->off_norms = take(ng * sizeof(GridNorm));
   P->off_inits = take(ng * sizeof(InitDev));
@@ -279,9 +314,20 @@ int refresh_active(jacobi_t* h, cudaStream_t s) {
     }
   }
   h->active_block_items.push_back((int32_t)h->active_items.size());
-  if (!h->active_items.empty())
+  // The same items grouped by kind (stable), for one kernel variant per kind.
+  h->kind_items.clear();
+  for (int k = 0; k < kItemKinds; ++k) {
+    h->kind_off[k] = (int32_t)h->kind_items.size();
+    for (const WorkItem& w : h->active_items)
+      if (item_kind(w) == k) h->kind_items.push_back(w);
+  }
+  h->kind_off[kItemKinds] = (int32_t)h->kind_items.size();
+  if (!h->active_items.empty()) {
     JGB_CUDA(cudaMemcpyAsync(h->d_active, h->active_items.data(), h->active_items.size() * sizeof(WorkItem),
                              cudaMemcpyHostToDevice, s));
+    JGB_CUDA(cudaMemcpyAsync(h->d_kind, h->kind_items.data(), h->kind_items.size() * sizeof(WorkItem),
+                             cudaMemcpyHostToDevice, s));
+  }
   if (!h->active_blocks.empty()) {
     JGB_CUDA(cudaMemcpyAsync(h->d_pblock_ids, h->active_blocks.data(), h->active_blocks.size() * sizeof(int32_t),
                              cudaMemcpyHostToDevice, s));
@@ -299,12 +345,19 @@ int refresh_active(jacobi_t* h, cudaStream_t s) {
 StepLaunch step_args(jacobi_t* h, int64_t it, bool all_items) {
   StepLaunch a;
   a.blocks = h->d_blocks;
-  a.items = all_items ? h->d_items : h->d_active;
-  a.n_items = all_items ? (int32_t)h->plan.items.size() : (int32_t)h->active_items.size();
+  // The full list (table order) serves the |b| kernel; steps use the active
+  // items grouped by kind.
+  a.items = all_items ? h->d_items : h->d_kind;
+  a.n_items = all_items ? (int32_t)h->plan.items.size() : (int32_t)h->kind_items.size();
+  for (int k = 0; k <= kItemKinds; ++k) a.kind_off[k] = all_items ? 0 : h->kind_off[k];
   a.grids = h->d_grids;
   a.it = it;
   a.partials = h->d_partials;
   a.dtype = h->plan.dtype;
+  a.stages = h->stages;
+  a.smem = 128 + h->stages * (int32_t)h->plan.max_stage;
+  a.err = h->d_err;
+  a.wait_ns = h->wait_ns;
   return a;
 }
 
@@ -371,7 +424,8 @@ int step_graph(jacobi_t* h, int64_t it0, int64_t n, cudaStream_t s) {
 }
 
 int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaStream_t s) {
-  const int maxc = persistent_max_ctas(h->plan.dtype);
+  const int smem = 128 + h->stages * (int32_t)h->plan.max_stage;
+  const int maxc = persistent_max_ctas(h->plan.dtype, smem);
   if (maxc <= 0) return set_error(JACOBI_ECUDA, "occupancy query for the persistent kernel failed");
   PersistLaunch a;
   a.blocks = h->d_blocks;
@@ -388,6 +442,8 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
   a.partials = h->d_partials;
   a.resid_first = resid_first ? 1 : 0;
   a.dtype = h->plan.dtype;
+  a.stages = h->stages;
+  a.smem = smem;
   const int ctas = std::min(maxc, a.n_blocks);
   JGB_CUDA(launch_persistent(a, ctas, s));
   return JACOBI_OK;
@@ -607,6 +663,7 @@ int jacobi_create_batch(int64_t n_grids, const jacobi_dim3* grids, const jacobi_
   h->d_geom = (BlockGeom*)(h->ws + P.off_geom);
   h->d_items = (WorkItem*)(h->ws + P.off_items);
   h->d_active = (WorkItem*)(h->ws + P.off_active);
+  h->d_kind = (WorkItem*)(h->ws + P.off_kind);
   h->d_grids = (GridDev*)(h->ws + P.off_grids);
   h->d_norms = (GridNorm*)(h->ws + P.off_norms);
   h->d_inits = (InitDev*)(h->ws + P.off_inits);
@@ -621,6 +678,15 @@ int jacobi_create_batch(int64_t n_grids, const jacobi_dim3* grids, const jacobi_
     const double ms = atof(w);
     if (ms > 0) h->wait_ns = (uint64_t)(ms * 1e6);
   }
+  // Ring depth of the plane-streaming path: FP32 is bandwidth-bound and wants
+  // two planes in flight per CTA; FP64 is bound by the FP64 pipe and prefers
+  // a shallower ring so that two CTAs fit on an SM.
+  h->stages = P.dtype == JACOBI_F64 ? 3 : 4;
+  if (const char* st = getenv("JACOBI_STAGES")) {
+    const int v = atoi(st);
+    if (v >= 3 && v <= 8) h->stages = v;
+  }
+  if (128 + h->stages * (int64_t)P.max_stage > kMaxStepSmem) h->stages = 3;
   rc = upload_tables(h, s);
   if (rc) return fail(rc);
   e = launch_init(h->d_blocks, h->d_geom, (int32_t)P.blocks.size(), h->d_inits, P.dtype, s);

@@ -39,8 +39,11 @@ struct BlockDev {
   int32_t pad_[2];
 };
 
-// One CTA's share of a step: block `block`, x-y tile origin (x0, y0) and the
-// z-range [z0, z1).  `slot` indexes the reduction partials.
+// One CTA's share of a step over the z-range [z0, z1) of block `block`:
+//   x0 >= 0: the TX x TY tile of columns at (x0, y0);
+//   x0 <  0: whole x-y planes, streamed through shared memory, each thread
+//            computing y0 rows (1, 2, 4 or 8) of one 16-byte vector column.
+// `slot` indexes the reduction partials.
 struct WorkItem {
   int32_t block;
   int32_t slot;

@@ -1,14 +1,8 @@
-// Jacobi3D kernels for sm_103a: initial state, state scatter/gather, the fused
-// stencil step (stencil + face pack into the neighbours' receive slots +
-// FP64 residual), the explicit pack/copy exchange, the deterministic residual
-// reduction and the persistent kernel whose blocks signal their neighbours
-// through device-side progress flags.
-//
-// The arithmetic follows the Jacobi iteration of the paper's proxy
-// application (Sec. 4.3); the stencil is read as the mean of the six face
-// neighbours, summed as ((xm + xp) + (ym + yp)) + (zm + zp) and multiplied by
-// 1/6 rounded to the state type, every operation rounded on its own.
-#include <cooperative_groups.h>
+// Jacobi3D support kernels for sm_103a: initial state, state scatter/gather,
+// the |b| partials, the deterministic per-grid reduction and the explicit
+// pack/copy form of the halo exchange.  The stencil step kernels (Sec. 4.3
+// Jacobi iteration, fused face pack, FP64 residual, persistent driver) are in
+// step.cu.
 
 #include "kernels.cuh"
 
@@ -155,116 +149,39 @@ __global__ void k_gather(const BlockDev* __restrict__ blocks, const BlockGeom* _
   }
 }
 
-// ---------------------------------------------------------------------------
-// The stencil sweep of one x-y tile of one block over planes [z0, z1).
-// Thread (tx, ty) owns column (x0 + tx, y0 + ty) and walks z with the planes
-// k-1, k, k+1 of its column in registers.  Neighbours across a block face are
-// read from that face's receive slot (parity p); with kPack the new boundary
-// planes are written into the neighbours' receive slots (parity p ^ 1).
-// Returns this thread's sum of r^2 (FP64) when kResid is set.
-// ---------------------------------------------------------------------------
-template <typename T, int MODE>
-__device__ __forceinline__ double tile_sweep(const BlockDev& B, int p, int x0, int y0, int z0, int z1) {
-  const int i = x0 + threadIdx.x, j = y0 + threadIdx.y;
-  const int nx = B.nx, ny = B.ny, nz = B.nz;
-  double acc = 0.0;
-  if (i >= nx || j >= ny) return acc;
-  const T* __restrict__ U = (const T*)B.u[p];
-  T* __restrict__ V = (T*)B.u[p ^ 1];
-  const int64_t pp = B.plane_pitch;
-  const T* rxm = (const T*)B.recv[XM][p];
-  const T* rxp = (const T*)B.recv[XP][p];
-  const T* rym = (const T*)B.recv[YM][p];
-  const T* ryp = (const T*)B.recv[YP][p];
-  const int64_t col = (int64_t)j * nx + i;
-  T below = (z0 == 0) ? __ldcg((const T*)B.recv[ZM][p] + col) : U[(int64_t)(z0 - 1) * pp + col];
-  T cur = U[(int64_t)z0 * pp + col];
-  const T* rzp = (const T*)B.recv[ZP][p];
-  T* sxm = nullptr; T* sxp = nullptr; T* sym = nullptr; T* syp = nullptr; T* szm = nullptr; T* szp = nullptr;
-  if (MODE & kPack) {
-    if (i == 0) sxm = (T*)B.send[XM][p ^ 1];
-    if (i == nx - 1) sxp = (T*)B.send[XP][p ^ 1];
-    if (j == 0) sym = (T*)B.send[YM][p ^ 1];
-    if (j == ny - 1) syp = (T*)B.send[YP][p ^ 1];
-    szm = (T*)B.send[ZM][p ^ 1];
-    szp = (T*)B.send[ZP][p ^ 1];
-  }
-  for (int k = z0; k < z1; ++k) {
-    const int64_t o = (int64_t)k * pp + col;
-    const T above = (k + 1 < nz) ? U[o + pp] : __ldcg(rzp + col);
-    const T xm = (i > 0) ? U[o - 1] : __ldcg(rxm + (int64_t)k * ny + j);
-    const T xp = (i < nx - 1) ? U[o + 1] : __ldcg(rxp + (int64_t)k * ny + j);
-    const T ym = (j > 0) ? U[o - nx] : __ldcg(rym + (int64_t)k * nx + i);
-    const T yp = (j < ny - 1) ? U[o + nx] : __ldcg(ryp + (int64_t)k * nx + i);
-    const T s = radd(radd(radd(xm, xp), radd(ym, yp)), radd(below, above));
-    if (MODE & kWrite) {
-      const T v = rmul(s, C6<T>::v);
-      V[o] = v;
-      if (MODE & kPack) {
-        if (sxm) sxm[(int64_t)k * ny + j] = v;
-        if (sxp) sxp[(int64_t)k * ny + j] = v;
-        if (sym) sym[(int64_t)k * nx + i] = v;
-        if (syp) syp[(int64_t)k * nx + i] = v;
-        if (k == 0 && szm) szm[col] = v;
-        if (k == nz - 1 && szp) szp[col] = v;
-      }
-    }
-    if (MODE & kResid) {
-      double s64;
-      if (sizeof(T) == 8) {
-        s64 = (double)s;
-      } else {
-        s64 = __dadd_rn(__dadd_rn(__dadd_rn((double)xm, (double)xp), __dadd_rn((double)ym, (double)yp)),
-                        __dadd_rn((double)below, (double)above));
-      }
-      const double r = __dsub_rn(s64, __dmul_rn(6.0, (double)cur));
-      acc = fma(r, r, acc);
-    }
-    below = cur;
-    cur = above;
-  }
-  return acc;
-}
-
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kThreads) k_step(StepLaunch a) {
-  const WorkItem w = a.items[blockIdx.x];
-  const BlockDev& B = a.blocks[w.block];
-  const int p = (int)((a.it - a.grids[B.grid].start_iter) & 1);
-  const double acc = tile_sweep<T, MODE>(B, p, w.x0, w.y0, w.z0, w.z1);
-  if (MODE & kResid) {
-    __shared__ double red[kThreads / 32];
-    const double s = block_sum<kThreads>(acc, red);
-    if (threadIdx.x == 0 && threadIdx.y == 0) a.partials[w.slot] = s;
-  }
-}
-
 // |b|^2 partials: the residual expression with every interior value set to 0,
-// so only Dirichlet ghosts contribute.
+// so only Dirichlet ghosts contribute.  A work item is either one TX x TY tile
+// (x0 >= 0) or a whole x-y plane range of its block (x0 < 0).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_bnorm(StepLaunch a) {
   const WorkItem w = a.items[blockIdx.x];
   const BlockDev& B = a.blocks[w.block];
   const int p = (int)((a.it - a.grids[B.grid].start_iter) & 1);
-  const int i = w.x0 + threadIdx.x, j = w.y0 + threadIdx.y;
   const int nx = B.nx, ny = B.ny, nz = B.nz;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int xa = w.x0 >= 0 ? w.x0 : 0, ya = w.x0 >= 0 ? w.y0 : 0;
+  const int xb = w.x0 >= 0 ? w.x0 + TX : nx, yb = w.x0 >= 0 ? w.y0 + TY : ny;
   double acc = 0.0;
-  if (i < nx && j < ny) {
-    for (int k = w.z0; k < w.z1; ++k) {
-      double v[6] = {0, 0, 0, 0, 0, 0};
-      if (i == 0 && B.nbr[XM] < 0) v[0] = (double)((const T*)B.recv[XM][p])[(int64_t)k * ny + j];
-      if (i == nx - 1 && B.nbr[XP] < 0) v[1] = (double)((const T*)B.recv[XP][p])[(int64_t)k * ny + j];
-      if (j == 0 && B.nbr[YM] < 0) v[2] = (double)((const T*)B.recv[YM][p])[(int64_t)k * nx + i];
-      if (j == ny - 1 && B.nbr[YP] < 0) v[3] = (double)((const T*)B.recv[YP][p])[(int64_t)k * nx + i];
-      if (k == 0 && B.nbr[ZM] < 0) v[4] = (double)((const T*)B.recv[ZM][p])[(int64_t)j * nx + i];
-      if (k == nz - 1 && B.nbr[ZP] < 0) v[5] = (double)((const T*)B.recv[ZP][p])[(int64_t)j * nx + i];
-      const double sb = __dadd_rn(__dadd_rn(__dadd_rn(v[0], v[1]), __dadd_rn(v[2], v[3])), __dadd_rn(v[4], v[5]));
-      acc = fma(sb, sb, acc);
+  for (int y0 = ya; y0 < yb; y0 += TY)
+    for (int x0 = xa; x0 < xb; x0 += TX) {
+      const int i = x0 + tx, j = y0 + ty;
+      if (i >= nx || j >= ny) continue;
+      for (int k = w.z0; k < w.z1; ++k) {
+        double v[6] = {0, 0, 0, 0, 0, 0};
+        if (i == 0 && B.nbr[XM] < 0) v[0] = (double)((const T*)B.recv[XM][p])[(int64_t)k * ny + j];
+        if (i == nx - 1 && B.nbr[XP] < 0) v[1] = (double)((const T*)B.recv[XP][p])[(int64_t)k * ny + j];
+        if (j == 0 && B.nbr[YM] < 0) v[2] = (double)((const T*)B.recv[YM][p])[(int64_t)k * nx + i];
+        if (j == ny - 1 && B.nbr[YP] < 0) v[3] = (double)((const T*)B.recv[YP][p])[(int64_t)k * nx + i];
+        if (k == 0 && B.nbr[ZM] < 0) v[4] = (double)((const T*)B.recv[ZM][p])[(int64_t)j * nx + i];
+        if (k == nz - 1 && B.nbr[ZP] < 0) v[5] = (double)((const T*)B.recv[ZP][p])[(int64_t)j * nx + i];
+        const double sb =
+            __dadd_rn(__dadd_rn(__dadd_rn(v[0], v[1]), __dadd_rn(v[2], v[3])), __dadd_rn(v[4], v[5]));
+        acc = fma(sb, sb, acc);
+      }
     }
-  }
   __shared__ double red[kThreads / 32];
   const double s = block_sum<kThreads>(acc, red);
-  if (threadIdx.x == 0 && threadIdx.y == 0) a.partials[w.slot] = s;
+  if (threadIdx.x == 0) a.partials[w.slot] = s;
 }
 
 // One warp per grid: lane l sums slots item_begin + l, + l + 32, ... in order,
@@ -326,84 +243,12 @@ __global__ void k_copy_faces(const BlockDev* __restrict__ blocks, void* const* s
   for (int64_t e = threadIdx.x; e < n; e += blockDim.x) D[e] = S[e];
 }
 
-// ---------------------------------------------------------------------------
-// Persistent kernel: CTA c owns active blocks c, c + G, c + 2G, ... for all
-// n_iters iterations.  Before block b computes iteration it (> it0) its CTA
-// acquire-waits until every neighbour's progress flag reaches it (the
-// neighbour finished iteration it - 1, so its faces of u_it are in b's slots
-// and it no longer reads the slots b is about to overwrite); after b's sweep
-// the CTA release-stores progress[b] = it + 1.  Waits are bounded: on expiry
-// the error word is set and every CTA leaves at its next wait.
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_persist(PersistLaunch a) {
-  __shared__ double red[kThreads / 32];
-  __shared__ int s_ok;
-  const int tid = threadIdx.y * TX + threadIdx.x;
-  for (int64_t t = 0; t < a.n_iters; ++t) {
-    const int64_t it = a.it0 + t;
-    for (int bi = blockIdx.x; bi < a.n_blocks; bi += gridDim.x) {
-      const int b = a.block_ids[bi];
-      const BlockDev& B = a.blocks[b];
-      if (t > 0) {
-        if (tid == 0) {
-          bool ok = true;
-          for (int f = 0; f < 6 && ok; ++f) {
-            const int nb = B.nbr[f];
-            if (nb >= 0) ok = wait_ge(a.progress + nb, it, a.err, a.wait_ns);
-          }
-          s_ok = ok ? 1 : 0;
-        }
-        __syncthreads();
-        if (!s_ok) return;
-      }
-      const int p = (int)((it - a.grids[B.grid].start_iter) & 1);
-      const bool resid = a.resid_first && t == 0;
-      for (int q = a.block_items[bi]; q < a.block_items[bi + 1]; ++q) {
-        const WorkItem w = a.items[q];
-        if (resid) {
-          const double acc = tile_sweep<T, kWrite | kPack | kResid>(B, p, w.x0, w.y0, w.z0, w.z1);
-          const double s = block_sum<kThreads>(acc, red);
-          if (tid == 0) a.partials[w.slot] = s;
-        } else {
-          tile_sweep<T, kWrite | kPack>(B, p, w.x0, w.y0, w.z0, w.z1);
-        }
-      }
-      __syncthreads();
-      if (tid == 0) {
-        __threadfence();
-        st_release(a.progress + b, it + 1);
-      }
-    }
-  }
-}
-
-template <typename T>
-cudaError_t launch_step_t(const StepLaunch& a, int mode, cudaStream_t s) {
-  if (a.n_items <= 0) return cudaSuccess;
-  const dim3 blk(TX, TY);
-  switch (mode) {
-    case kWrite | kPack: k_step<T, kWrite | kPack><<<a.n_items, blk, 0, s>>>(a); break;
-    case kWrite | kPack | kResid: k_step<T, kWrite | kPack | kResid><<<a.n_items, blk, 0, s>>>(a); break;
-    case kWrite: k_step<T, kWrite><<<a.n_items, blk, 0, s>>>(a); break;
-    case kWrite | kResid: k_step<T, kWrite | kResid><<<a.n_items, blk, 0, s>>>(a); break;
-    case kResid: k_step<T, kResid><<<a.n_items, blk, 0, s>>>(a); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
-
 }  // namespace
-
-cudaError_t launch_step(const StepLaunch& a, int mode, cudaStream_t s) {
-  return a.dtype == 0 ? launch_step_t<double>(a, mode, s) : launch_step_t<float>(a, mode, s);
-}
 
 cudaError_t launch_bnorm(const StepLaunch& a, cudaStream_t s) {
   if (a.n_items <= 0) return cudaSuccess;
-  const dim3 blk(TX, TY);
-  if (a.dtype == 0) k_bnorm<double><<<a.n_items, blk, 0, s>>>(a);
-  else k_bnorm<float><<<a.n_items, blk, 0, s>>>(a);
+  if (a.dtype == 0) k_bnorm<double><<<a.n_items, kThreads, 0, s>>>(a);
+  else k_bnorm<float><<<a.n_items, kThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -464,26 +309,6 @@ cudaError_t launch_gather(const BlockDev* blocks, const BlockGeom* geom, int32_t
   if (dtype == 0) k_gather<double><<<grid, 256, 0, s>>>(blocks, geom, b0, (double*)dst, NX, NY, parity, padded);
   else k_gather<float><<<grid, 256, 0, s>>>(blocks, geom, b0, (float*)dst, NX, NY, parity, padded);
   return cudaGetLastError();
-}
-
-int persistent_max_ctas(int dtype) {
-  int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  cudaError_t e = dtype == 0
-                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<double>, kThreads, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float>, kThreads, 0);
-  if (e != cudaSuccess) return 0;
-  return per_sm * sms;
-}
-
-cudaError_t launch_persistent(const PersistLaunch& a, int grid_ctas, cudaStream_t s) {
-  if (a.n_blocks <= 0 || a.n_iters <= 0) return cudaSuccess;
-  PersistLaunch args = a;
-  void* params[] = {&args};
-  const dim3 blk(TX, TY);
-  const void* fn = a.dtype == 0 ? (const void*)k_persist<double> : (const void*)k_persist<float>;
-  return cudaLaunchCooperativeKernel(fn, dim3(grid_ctas), blk, params, 0, s);
 }
 
 }  // namespace jgb

@@ -22,14 +22,30 @@ struct BlockGeom {
   int32_t grid;
 };
 
+// Largest dynamic shared memory a step kernel may use (sm_103a opt-in limit of
+// 227 KB per CTA, minus room for the kernels' static shared memory).
+constexpr int kMaxStepSmem = 227 * 1024 - 1024;  // 1 KB left for static shared memory
+
+// Item kinds of a step launch: 0 = tiles, 1..4 = plane streaming with 1, 2,
+// 4, 8 rows per thread.  Each kind runs its own kernel variant.
+constexpr int kItemKinds = 5;
+__host__ __device__ inline int item_kind(const WorkItem& w) {
+  return w.x0 >= 0 ? 0 : (w.y0 == 1 ? 1 : w.y0 == 2 ? 2 : w.y0 == 4 ? 3 : 4);
+}
+
 struct StepLaunch {
   const BlockDev* blocks;
-  const WorkItem* items;  // active items
+  const WorkItem* items;  // active items, grouped by kind
   int32_t n_items;
+  int32_t kind_off[kItemKinds + 1];  // items of kind k: [kind_off[k], kind_off[k+1])
   const GridDev* grids;
   int64_t it;             // global iteration being computed (u_it -> u_it+1)
   double* partials;       // per item slot
   int32_t dtype;          // 0 = f64, 1 = f32
+  int32_t stages;         // ring stages of the plane-streaming path
+  int32_t smem;           // dynamic shared memory bytes (128 + stages * max stage)
+  uint32_t* err;          // device error word (bounded waits)
+  uint64_t wait_ns;
 };
 
 // Step kernels.  mode flags:
@@ -80,8 +96,10 @@ struct PersistLaunch {
   double* partials;
   int32_t resid_first;         // fuse the residual of u_it0 into the first iteration
   int32_t dtype;
+  int32_t stages;
+  int32_t smem;
 };
 cudaError_t launch_persistent(const PersistLaunch& a, int grid_ctas, cudaStream_t s);
-int persistent_max_ctas(int dtype);  // co-resident CTA limit (0 on error)
+int persistent_max_ctas(int dtype, int smem);  // co-resident CTA limit (0 on error)
 
 }  // namespace jgb

@@ -59,8 +59,9 @@ struct Plan {
   std::vector<WorkItem> items;
   int64_t n_points = 0;
   int64_t halo_elems = 0;  // face elements moved per iteration (internal faces)
+  uint32_t max_stage = 0;  // largest ring stage (bytes) of a plane-streamed block
   // byte offsets into the workspace
-  size_t off_blocks, off_geom, off_items, off_active, off_grids, off_norms, off_inits, off_gids, off_partials,
+  size_t off_blocks, off_geom, off_items, off_active, off_kind, off_grids, off_norms, off_inits, off_gids, off_partials,
       off_progress, off_err, off_stage_tab, off_pblock_items, off_pblock_ids;
   size_t bytes = 0;
 };
@@ -85,6 +86,7 @@ struct jacobi_s {
   jgb::BlockGeom* d_geom = nullptr;
   jgb::WorkItem* d_items = nullptr;
   jgb::WorkItem* d_active = nullptr;
+  jgb::WorkItem* d_kind = nullptr;
   jgb::GridDev* d_grids = nullptr;
   jgb::GridNorm* d_norms = nullptr;
   jgb::InitDev* d_inits = nullptr;
@@ -101,6 +103,8 @@ struct jacobi_s {
   std::vector<int32_t> active_blocks;       // block ids of active grids (item-grouped)
   std::vector<int32_t> active_block_items;  // n_active_blocks + 1 offsets into active_items
   std::vector<int32_t> active_grids;
+  std::vector<jgb::WorkItem> kind_items;        // active items grouped by kind
+  int32_t kind_off[jgb::kItemKinds + 1] = {};
   bool tables_dirty = true;
   jgb::GridDev* h_grids = nullptr;   // pinned, uploaded to d_grids
   jgb::GridNorm* h_norms = nullptr;  // pinned, read back from d_norms
@@ -112,6 +116,7 @@ struct jacobi_s {
   int32_t graph_items = -1;
 
   uint64_t wait_ns = 1000000000ull;
+  int32_t stages = 4;             // ring stages of the plane-streaming path
   int64_t drop_block = -1;        // fault injection (persistent path)
   void* stage = nullptr;          // device staging for host transfers
   size_t stage_bytes = 0;

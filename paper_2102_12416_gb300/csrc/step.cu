@@ -1,0 +1,645 @@
+// Jacobi3D step kernels for sm_103a: the stencil update of the paper's proxy
+// application (Sec. 4.3, Jacobi iteration on a 3D grid split into blocks that
+// exchange halos with up to six neighbours every iteration), with the face
+// pack fused into the epilogue (new boundary planes are stored straight into
+// the neighbours' receive slots, the intra-device form of the Channel API of
+// Sec. 3.2.2) and the FP64 residual fused in on check iterations.
+//
+// Stencil reading: u' = (((xm + xp) + (ym + yp)) + (zm + zp)) * c6, c6 = 1/6
+// rounded to the state type, every operation rounded on its own (no FMA), so
+// FP64 results are bit-exact with a monolithic CPU evaluation in that order.
+//
+// Two ways to sweep a work item:
+//  * plane streaming (x0 < 0): the CTA owns whole x-y planes of one block over
+//    [z0, z1).  One elected thread fills a ring of shared-memory stages with
+//    1D bulk copies (cp.async.bulk, completion counted by an mbarrier
+//    transaction count): each stage holds one plane plus the four x/y ghost
+//    vectors of that plane from the receive slots; the z ghosts come in as
+//    whole planes from the z slots.  Each thread computes a VEC x RY patch
+//    (VEC = one 16-byte vector along x) from shared memory and stores it with
+//    16-byte stores.  Blocks whose shape does not fit take the next path.
+//  * tiles (x0 >= 0): a TX x TY tile of columns, one column per thread, read
+//    straight from global memory with the z neighbours in registers.
+#include "kernels.cuh"
+
+namespace jgb {
+
+namespace {
+
+// ---- mbarrier / bulk-copy helpers -------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(b))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.b32 %0, 1, 0, P;\n}"
+      : "=r"(r)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return r != 0;
+}
+// Bounded wait for the phase of parity `parity`; on expiry records DEV_TIMEOUT.
+__device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint32_t* err, uint64_t limit_ns) {
+  if (mbar_test(b, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t n = 0; n < (1u << 26); ++n) {
+    if (mbar_test(b, parity)) return true;
+    if (globaltimer_ns() - t0 > limit_ns) break;
+  }
+  atomicCAS(err, (uint32_t)DEV_OK, (uint32_t)DEV_TIMEOUT);
+  return false;
+}
+
+// ---- 16-byte vectors ---------------------------------------------------------
+template <typename T> struct V16;
+template <> struct V16<float> {
+  static constexpr int N = 4;
+  __device__ static __forceinline__ void load(const float* p, float (&v)[4]) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  }
+  __device__ static __forceinline__ void store(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <> struct V16<double> {
+  static constexpr int N = 2;
+  __device__ static __forceinline__ void load(const double* p, double (&v)[2]) {
+    const double2 x = *reinterpret_cast<const double2*>(p);
+    v[0] = x.x; v[1] = x.y;
+  }
+  __device__ static __forceinline__ void store(double* p, const double (&v)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+};
+
+// FP64 residual contribution of one point: r = s - 6u with s re-evaluated in
+// FP64 from the (exactly widened) neighbours in the stencil's order.
+template <typename T>
+__device__ __forceinline__ double resid2(T xm, T xp, T ym, T yp, T zm, T zp, T s, T c) {
+  double s64;
+  if (sizeof(T) == 8) {
+    s64 = (double)s;
+  } else {
+    s64 = __dadd_rn(__dadd_rn(__dadd_rn((double)xm, (double)xp), __dadd_rn((double)ym, (double)yp)),
+                    __dadd_rn((double)zm, (double)zp));
+  }
+  const double r = __dsub_rn(s64, __dmul_rn(6.0, (double)c));
+  return r * r;
+}
+
+// ---------------------------------------------------------------------------
+// Tile path: thread (tx, ty) owns column (x0 + tx, y0 + ty) of block B and
+// walks planes [z0, z1) with k-1, k, k+1 of its column in registers.
+// Neighbours across a block face come from that face's receive slot (parity
+// p); with kPack the new boundary planes go to the neighbours' slots (p ^ 1).
+// ---------------------------------------------------------------------------
+template <typename T, int MODE>
+__device__ __forceinline__ double tile_sweep(const BlockDev& B, int p, int x0, int y0, int z0, int z1, int tx,
+                                             int ty) {
+  const int i = x0 + tx, j = y0 + ty;
+  const int nx = B.nx, ny = B.ny, nz = B.nz;
+  double acc = 0.0;
+  if (i >= nx || j >= ny) return acc;
+  const T* __restrict__ U = (const T*)B.u[p];
+  T* __restrict__ V = (T*)B.u[p ^ 1];
+  const int64_t pp = B.plane_pitch;
+  const T* rxm = (const T*)B.recv[XM][p];
+  const T* rxp = (const T*)B.recv[XP][p];
+  const T* rym = (const T*)B.recv[YM][p];
+  const T* ryp = (const T*)B.recv[YP][p];
+  const T* rzp = (const T*)B.recv[ZP][p];
+  const int64_t col = (int64_t)j * nx + i;
+  T below = (z0 == 0) ? __ldcg((const T*)B.recv[ZM][p] + col) : U[(int64_t)(z0 - 1) * pp + col];
+  T cur = U[(int64_t)z0 * pp + col];
+  T* sxm = nullptr; T* sxp = nullptr; T* sym = nullptr; T* syp = nullptr; T* szm = nullptr; T* szp = nullptr;
+  if (MODE & kPack) {
+    if (i == 0) sxm = (T*)B.send[XM][p ^ 1];
+    if (i == nx - 1) sxp = (T*)B.send[XP][p ^ 1];
+    if (j == 0) sym = (T*)B.send[YM][p ^ 1];
+    if (j == ny - 1) syp = (T*)B.send[YP][p ^ 1];
+    szm = (T*)B.send[ZM][p ^ 1];
+    szp = (T*)B.send[ZP][p ^ 1];
+  }
+  for (int k = z0; k < z1; ++k) {
+    const int64_t o = (int64_t)k * pp + col;
+    const T above = (k + 1 < nz) ? U[o + pp] : __ldcg(rzp + col);
+    const T xm = (i > 0) ? U[o - 1] : __ldcg(rxm + (int64_t)k * ny + j);
+    const T xp = (i < nx - 1) ? U[o + 1] : __ldcg(rxp + (int64_t)k * ny + j);
+    const T ym = (j > 0) ? U[o - nx] : __ldcg(rym + (int64_t)k * nx + i);
+    const T yp = (j < ny - 1) ? U[o + nx] : __ldcg(ryp + (int64_t)k * nx + i);
+    const T s = radd(radd(radd(xm, xp), radd(ym, yp)), radd(below, above));
+    if (MODE & kWrite) {
+      const T v = rmul(s, C6<T>::v);
+      V[o] = v;
+      if (MODE & kPack) {
+        if (sxm) sxm[(int64_t)k * ny + j] = v;
+        if (sxp) sxp[(int64_t)k * ny + j] = v;
+        if (sym) sym[(int64_t)k * nx + i] = v;
+        if (syp) syp[(int64_t)k * nx + i] = v;
+        if (k == 0 && szm) szm[col] = v;
+        if (k == nz - 1 && szp) szp[col] = v;
+      }
+    }
+    if (MODE & kResid) acc += resid2<T>(xm, xp, ym, yp, below, above, s, cur);
+    below = cur;
+    cur = above;
+  }
+  return acc;
+}
+
+// ---------------------------------------------------------------------------
+// Plane-streaming path.
+// ---------------------------------------------------------------------------
+struct Ring {
+  unsigned char* stages;
+  uint64_t* bars;
+  int S;
+  uint32_t pbits;  // parity of each stage's next fill (bit st)
+};
+
+// Compute plane q of the item (k = z0 - 1 + q) from the stages holding planes
+// q - 1, q, q + 1.  Thread layout: tx = vector column, ty = group of RY rows.
+template <typename T, int RY, int MODE>
+__device__ __forceinline__ double stream_plane(const BlockDev& B, int p, int k, const unsigned char* sm,
+                                               const unsigned char* sc, const unsigned char* sp, int tx, int ty) {
+  constexpr int VEC = V16<T>::N;
+  const int nx = B.nx, ny = B.ny, nz = B.nz;
+  const int i0 = tx * VEC, j0 = ty * RY;
+  const size_t plane_bytes = (size_t)nx * ny * sizeof(T);
+  const T* Pm = (const T*)sm;
+  const T* Pc = (const T*)sc;
+  const T* Pp = (const T*)sp;
+  const T* Gxm = (const T*)(sc + plane_bytes);
+  const T* Gxp = Gxm + ny;
+  const T* Gym = Gxp + ny;
+  const T* Gyp = Gym + nx;
+  T* __restrict__ V = (T*)B.u[p ^ 1] + (int64_t)k * B.plane_pitch;
+
+  T c[RY][VEC];
+#pragma unroll
+  for (int r = 0; r < RY; ++r) V16<T>::load(Pc + (j0 + r) * nx + i0, c[r]);
+  T top[VEC], bot[VEC];
+  V16<T>::load(j0 > 0 ? Pc + (j0 - 1) * nx + i0 : Gym + i0, top);
+  V16<T>::load(j0 + RY < ny ? Pc + (j0 + RY) * nx + i0 : Gyp + i0, bot);
+  double acc = 0.0;
+#pragma unroll
+  for (int r = 0; r < RY; ++r) {
+    const int j = j0 + r;
+    T zm[VEC], zp[VEC];
+    V16<T>::load(Pm + j * nx + i0, zm);
+    V16<T>::load(Pp + j * nx + i0, zp);
+    const T* ym = r == 0 ? top : c[r > 0 ? r - 1 : 0];
+    const T* yp = r == RY - 1 ? bot : c[r < RY - 1 ? r + 1 : 0];
+    const T left = i0 > 0 ? Pc[j * nx + i0 - 1] : Gxm[j];
+    const T right = i0 + VEC < nx ? Pc[j * nx + i0 + VEC] : Gxp[j];
+    T v[VEC];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) {
+      const T xm = q == 0 ? left : c[r][q > 0 ? q - 1 : 0];
+      const T xp = q == VEC - 1 ? right : c[r][q < VEC - 1 ? q + 1 : 0];
+      const T s = radd(radd(radd(xm, xp), radd(ym[q], yp[q])), radd(zm[q], zp[q]));
+      v[q] = rmul(s, C6<T>::v);
+      if (MODE & kResid) acc += resid2<T>(xm, xp, ym[q], yp[q], zm[q], zp[q], s, c[r][q]);
+    }
+    if (MODE & kWrite) {
+      V16<T>::store(V + j * nx + i0, v);
+      if (MODE & kPack) {
+        if (i0 == 0) {
+          T* d = (T*)B.send[XM][p ^ 1];
+          if (d) d[(int64_t)k * ny + j] = v[0];
+        }
+        if (i0 + VEC == nx) {
+          T* d = (T*)B.send[XP][p ^ 1];
+          if (d) d[(int64_t)k * ny + j] = v[VEC - 1];
+        }
+        if (j == 0) {
+          T* d = (T*)B.send[YM][p ^ 1];
+          if (d) V16<T>::store(d + (int64_t)k * nx + i0, v);
+        }
+        if (j == ny - 1) {
+          T* d = (T*)B.send[YP][p ^ 1];
+          if (d) V16<T>::store(d + (int64_t)k * nx + i0, v);
+        }
+        if (k == 0) {
+          T* d = (T*)B.send[ZM][p ^ 1];
+          if (d) V16<T>::store(d + j * nx + i0, v);
+        }
+        if (k == nz - 1) {
+          T* d = (T*)B.send[ZP][p ^ 1];
+          if (d) V16<T>::store(d + j * nx + i0, v);
+        }
+      }
+    }
+  }
+  return acc;
+}
+
+// Bytes of one ring stage for block B: the plane and its four x/y ghost
+// vectors, rounded up to 128 bytes.
+template <typename T>
+__device__ __forceinline__ uint32_t stage_bytes_of(const BlockDev& B) {
+  const uint32_t plane = (uint32_t)(B.nx * B.ny * sizeof(T));
+  const uint32_t g = (uint32_t)(2 * (B.nx + B.ny) * sizeof(T));
+  return (plane + g + 127u) & ~127u;
+}
+
+// Stream planes [z0, z1) of block B through the ring.  All threads of the CTA
+// call it.  Returns this thread's r^2 sum; sets ok = false (CTA-uniform) after
+// a bounded wait expired (the error word is set and issued copies drained).
+template <typename T, int RY, int MODE>
+__device__ double stream_item(const BlockDev& B, int p, int z0, int z1, Ring& ring, uint32_t* err,
+                              uint64_t wait_ns, bool& ok) {
+  constexpr int VEC = V16<T>::N;
+  const int nx = B.nx, ny = B.ny, nz = B.nz;
+  const int tid = threadIdx.x;
+  const int txv = nx / VEC;
+  const int tx = tid % txv, ty = tid / txv;
+  const bool active = ty * RY < ny;
+  const int S = ring.S;
+  const uint32_t sbytes = stage_bytes_of<T>(B);
+  const uint32_t plane_bytes = (uint32_t)(nx * ny * sizeof(T));
+  const uint32_t xg = (uint32_t)(ny * sizeof(T)), yg = (uint32_t)(nx * sizeof(T));
+  const T* U = (const T*)B.u[p];
+  const int nplanes = z1 - z0 + 2;  // planes z0-1 .. z1
+
+  auto issue = [&](int q) {
+    const int st = q % S;
+    unsigned char* dst = ring.stages + (size_t)st * sbytes;
+    const int kk = z0 - 1 + q;
+    const T* src = kk < 0 ? (const T*)B.recv[ZM][p] : (kk >= nz ? (const T*)B.recv[ZP][p] : U + (int64_t)kk * B.plane_pitch);
+    const bool ghosts = q >= 1 && q <= nplanes - 2;
+    uint64_t* bar = ring.bars + st;
+    mbar_expect_tx(bar, plane_bytes + (ghosts ? 2 * (xg + yg) : 0));
+    bulk_g2s(dst, src, plane_bytes, bar);
+    if (ghosts) {
+      bulk_g2s(dst + plane_bytes, (const T*)B.recv[XM][p] + (int64_t)kk * ny, xg, bar);
+      bulk_g2s(dst + plane_bytes + xg, (const T*)B.recv[XP][p] + (int64_t)kk * ny, xg, bar);
+      bulk_g2s(dst + plane_bytes + 2 * xg, (const T*)B.recv[YM][p] + (int64_t)kk * nx, yg, bar);
+      bulk_g2s(dst + plane_bytes + 2 * xg + yg, (const T*)B.recv[YP][p] + (int64_t)kk * nx, yg, bar);
+    }
+  };
+  auto wait = [&](int q) {
+    const int st = q % S;
+    const uint32_t parity = ((ring.pbits >> st) ^ (uint32_t)(q / S)) & 1u;
+    return mbar_wait(ring.bars + st, parity, err, wait_ns);
+  };
+
+  int issued = 0;
+  if (tid == 0) {
+    fence_proxy_async();
+    const int n0 = min(S - 1, nplanes);
+    for (int q = 0; q < n0; ++q) issue(q);
+  }
+  issued = min(S - 1, nplanes);
+  double acc = 0.0;
+  bool good = true;
+  for (int q = 1; q <= nplanes - 2; ++q) {
+    // Every thread is done with plane q - 2 (read while computing q - 1).
+    if (!__syncthreads_and(good)) break;
+    const int qi = q - 2 + S;
+    if (qi < nplanes && qi >= issued) {
+      if (tid == 0) {
+        fence_proxy_async();
+        issue(qi);
+      }
+      issued = qi + 1;
+    }
+    if (q == 1) good = wait(0) && wait(1);
+    good = good && wait(q + 1);
+    if (good && active) {
+      const unsigned char* sm = ring.stages + (size_t)((q - 1) % S) * sbytes;
+      const unsigned char* sc = ring.stages + (size_t)(q % S) * sbytes;
+      const unsigned char* sp = ring.stages + (size_t)((q + 1) % S) * sbytes;
+      acc += stream_plane<T, RY, MODE>(B, p, z0 - 1 + q, sm, sc, sp, tx, ty);
+    }
+  }
+  ok = __syncthreads_and(good) != 0;
+  if (!ok && tid == 0) {
+    // Drain: wait (bounded) for the latest fill issued into each stage.
+    for (int st = 0; st < S; ++st) {
+      int qlast = -1;
+      for (int q = st; q < issued; q += S) qlast = q;
+      if (qlast >= 0) wait(qlast);
+    }
+  }
+  // advance the per-stage fill parities past this item's fills
+  for (int st = 0; st < S; ++st) {
+    const int fills = (nplanes > st) ? (nplanes - st + S - 1) / S : 0;
+    ring.pbits ^= (uint32_t)(fills & 1) << st;
+  }
+  return acc;
+}
+
+template <typename T, int MODE>
+__device__ double run_item(const BlockDev& B, int p, const WorkItem& w, Ring& ring, uint32_t* err,
+                           uint64_t wait_ns, bool& ok) {
+  ok = true;
+  if (w.x0 >= 0) return tile_sweep<T, MODE>(B, p, w.x0, w.y0, w.z0, w.z1, threadIdx.x % TX, threadIdx.x / TX);
+  switch (w.y0) {
+    case 1: return stream_item<T, 1, MODE>(B, p, w.z0, w.z1, ring, err, wait_ns, ok);
+    case 2: return stream_item<T, 2, MODE>(B, p, w.z0, w.z1, ring, err, wait_ns, ok);
+    case 4: return stream_item<T, 4, MODE>(B, p, w.z0, w.z1, ring, err, wait_ns, ok);
+    default: return stream_item<T, 8, MODE>(B, p, w.z0, w.z1, ring, err, wait_ns, ok);
+  }
+}
+
+__device__ __forceinline__ Ring ring_setup(unsigned char* smem, int S) {
+  Ring ring;
+  ring.bars = (uint64_t*)smem;
+  ring.stages = smem + 128;
+  ring.S = S;
+  ring.pbits = 0;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < S; ++st) mbar_init(ring.bars + st, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  return ring;
+}
+
+// Tile items (x0 >= 0), one TX x TY tile per CTA.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) k_tiles(StepLaunch a) {
+  const WorkItem w = a.items[blockIdx.x];
+  const BlockDev& B = a.blocks[w.block];
+  const int p = (int)((a.it - a.grids[B.grid].start_iter) & 1);
+  const double acc = tile_sweep<T, MODE>(B, p, w.x0, w.y0, w.z0, w.z1, threadIdx.x % TX, threadIdx.x / TX);
+  if (MODE & kResid) {
+    __shared__ double red[kThreads / 32];
+    const double s = block_sum<kThreads>(acc, red);
+    if (threadIdx.x == 0) a.partials[w.slot] = s;
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+
+// Plane-streaming items (x0 < 0), one item per CTA, warp-specialised: warp 8
+// is the producer (its lane 0 issues the bulk copies of plane q into stage
+// q % S once all consumer warps have released that stage through its "empty"
+// mbarrier), warps 0..7 are consumers (each waits on the "full" mbarrier of
+// the planes it needs, computes, and releases the stage of plane q - 1 after
+// computing plane q, its last use).  There is no CTA-wide barrier inside the
+// plane loop, so consumer warps drift freely within the ring.
+constexpr int kConsumerWarps = kThreads / 32;
+constexpr int kStreamThreads = kThreads + 32;
+
+template <typename T> struct StreamOcc;
+template <> struct StreamOcc<float> { static constexpr int min_blocks = 3; };
+template <> struct StreamOcc<double> { static constexpr int min_blocks = 2; };
+
+template <typename T, int RY, int MODE>
+__global__ void __launch_bounds__(kStreamThreads, StreamOcc<T>::min_blocks) k_stream(StepLaunch a) {
+  constexpr int VEC = V16<T>::N;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* full = (uint64_t*)smem;
+  uint64_t* empty = full + 8;
+  unsigned char* stages = smem + 128;
+  const WorkItem w = a.items[blockIdx.x];
+  const BlockDev& B = a.blocks[w.block];
+  const int p = (int)((a.it - a.grids[B.grid].start_iter) & 1);
+  const int S = a.stages;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nx = B.nx, ny = B.ny, nz = B.nz;
+  const int z0 = w.z0, z1 = w.z1;
+  const int nplanes = z1 - z0 + 2;  // planes z0-1 .. z1
+  const uint32_t sbytes = stage_bytes_of<T>(B);
+  if (tid == 0) {
+    for (int st = 0; st < S; ++st) {
+      mbar_init(full + st, 1);
+      mbar_init(empty + st, kConsumerWarps);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  double acc = 0.0;
+  if (warp == kConsumerWarps) {
+    // ---- producer ----
+    if (lane == 0) {
+      const uint32_t plane_bytes = (uint32_t)(nx * ny * sizeof(T));
+      const uint32_t xg = (uint32_t)(ny * sizeof(T)), yg = (uint32_t)(nx * sizeof(T));
+      const T* U = (const T*)B.u[p];
+      int q = 0;
+      for (; q < nplanes; ++q) {
+        const int st = q % S, fill = q / S;
+        if (fill > 0 && !mbar_wait(empty + st, (uint32_t)(fill - 1) & 1u, a.err, a.wait_ns)) break;
+        fence_proxy_async();
+        unsigned char* dst = stages + (size_t)st * sbytes;
+        const int kk = z0 - 1 + q;
+        const T* src = kk < 0 ? (const T*)B.recv[ZM][p]
+                              : (kk >= nz ? (const T*)B.recv[ZP][p] : U + (int64_t)kk * B.plane_pitch);
+        const bool ghosts = q >= 1 && q <= nplanes - 2;
+        uint64_t* bar = full + st;
+        mbar_expect_tx(bar, plane_bytes + (ghosts ? 2 * (xg + yg) : 0));
+        bulk_g2s(dst, src, plane_bytes, bar);
+        if (ghosts) {
+          bulk_g2s(dst + plane_bytes, (const T*)B.recv[XM][p] + (int64_t)kk * ny, xg, bar);
+          bulk_g2s(dst + plane_bytes + xg, (const T*)B.recv[XP][p] + (int64_t)kk * ny, xg, bar);
+          bulk_g2s(dst + plane_bytes + 2 * xg, (const T*)B.recv[YM][p] + (int64_t)kk * nx, yg, bar);
+          bulk_g2s(dst + plane_bytes + 2 * xg + yg, (const T*)B.recv[YP][p] + (int64_t)kk * nx, yg, bar);
+        }
+      }
+      if (q < nplanes) {
+        // A wait expired: let the copies already issued land before leaving.
+        for (int st = 0; st < S; ++st) {
+          int qlast = -1;
+          for (int r = st; r < q; r += S) qlast = r;
+          if (qlast >= 0) mbar_wait(full + st, (uint32_t)(qlast / S) & 1u, a.err, a.wait_ns);
+        }
+      }
+    }
+  } else {
+    // ---- consumers ----
+    const int txv = nx / VEC;
+    const int tx = tid % txv, ty = tid / txv;
+    const bool active = ty * RY < ny;
+    bool good = true;
+    for (int q = 1; q <= nplanes - 2 && good; ++q) {
+      if (q == 1) {
+        good = mbar_wait(full + 0, 0u, a.err, a.wait_ns) && mbar_wait(full + 1 % S, (uint32_t)(1 / S) & 1u, a.err, a.wait_ns);
+      }
+      good = good && mbar_wait(full + (q + 1) % S, (uint32_t)((q + 1) / S) & 1u, a.err, a.wait_ns);
+      good = __all_sync(0xffffffffu, good);
+      if (!good) break;
+      if (active) {
+        const unsigned char* sm = stages + (size_t)((q - 1) % S) * sbytes;
+        const unsigned char* sc = stages + (size_t)(q % S) * sbytes;
+        const unsigned char* sp = stages + (size_t)((q + 1) % S) * sbytes;
+        acc += stream_plane<T, RY, MODE>(B, p, z0 - 1 + q, sm, sc, sp, tx, ty);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty + (q - 1) % S);
+    }
+  }
+  if (MODE & kResid) {
+    __shared__ double red[kStreamThreads / 32];
+    const double s = block_sum<kStreamThreads>(acc, red);
+    if (tid == 0) a.partials[w.slot] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent kernel: CTA c owns active blocks c, c + G, c + 2G, ... for all
+// n_iters iterations.  Before block b computes iteration it (> it0) its CTA
+// acquire-waits until every neighbour's progress flag reaches it (the
+// neighbour finished iteration it - 1, so its faces of u_it are in b's slots
+// and it no longer reads the slots b is about to overwrite); after b's sweep
+// the CTA release-stores progress[b] = it + 1.  Waits are bounded: on expiry
+// the error word is set and every CTA leaves at its next wait.
+// Proxy fences order the generic stores of neighbours (and of this CTA's
+// previous iteration) before the bulk copies that read them.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_persist(PersistLaunch a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ double red[kThreads / 32];
+  __shared__ int s_ok;
+  const int tid = threadIdx.x;
+  Ring ring = ring_setup(smem, a.stages);
+  for (int64_t t = 0; t < a.n_iters; ++t) {
+    const int64_t it = a.it0 + t;
+    for (int bi = blockIdx.x; bi < a.n_blocks; bi += gridDim.x) {
+      const int b = a.block_ids[bi];
+      const BlockDev& B = a.blocks[b];
+      if (t > 0) {
+        if (tid == 0) {
+          bool okw = true;
+          for (int f = 0; f < 6 && okw; ++f) {
+            const int nb = B.nbr[f];
+            if (nb >= 0) okw = wait_ge(a.progress + nb, it, a.err, a.wait_ns);
+          }
+          fence_proxy_async();
+          s_ok = okw ? 1 : 0;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+      }
+      const int p = (int)((it - a.grids[B.grid].start_iter) & 1);
+      const bool resid = a.resid_first && t == 0;
+      for (int q = a.block_items[bi]; q < a.block_items[bi + 1]; ++q) {
+        const WorkItem w = a.items[q];
+        bool ok;
+        if (resid) {
+          const double acc = run_item<T, kWrite | kPack | kResid>(B, p, w, ring, a.err, a.wait_ns, ok);
+          const double s = block_sum<kThreads>(acc, red);
+          if (tid == 0) a.partials[w.slot] = s;
+        } else {
+          run_item<T, kWrite | kPack>(B, p, w, ring, a.err, a.wait_ns, ok);
+        }
+        if (!ok) return;  // CTA-uniform
+      }
+      fence_proxy_async();
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release(a.progress + b, it + 1);
+      }
+    }
+  }
+}
+
+template <typename K>
+cudaError_t set_smem_attr(K kernel, bool& done) {
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxStepSmem);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+template <typename T, int RY, int MODE>
+cudaError_t launch_stream(const StepLaunch& a, cudaStream_t s) {
+  static bool done = false;
+  cudaError_t e = set_smem_attr(k_stream<T, RY, MODE>, done);
+  if (e != cudaSuccess) return e;
+  k_stream<T, RY, MODE><<<a.n_items, kStreamThreads, a.smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+cudaError_t launch_kinds(const StepLaunch& a, cudaStream_t s) {
+  for (int kind = 0; kind < kItemKinds; ++kind) {
+    StepLaunch b = a;
+    b.items = a.items + a.kind_off[kind];
+    b.n_items = a.kind_off[kind + 1] - a.kind_off[kind];
+    if (b.n_items <= 0) continue;
+    cudaError_t e = cudaSuccess;
+    switch (kind) {
+      case 0: k_tiles<T, MODE><<<b.n_items, kThreads, 0, s>>>(b); e = cudaGetLastError(); break;
+      case 1: e = launch_stream<T, 1, MODE>(b, s); break;
+      case 2: e = launch_stream<T, 2, MODE>(b, s); break;
+      case 3: e = launch_stream<T, 4, MODE>(b, s); break;
+      default: e = launch_stream<T, 8, MODE>(b, s); break;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_step_t(const StepLaunch& a, int mode, cudaStream_t s) {
+  if (a.n_items <= 0) return cudaSuccess;
+  switch (mode) {
+    case kWrite | kPack: return launch_kinds<T, kWrite | kPack>(a, s);
+    case kWrite | kPack | kResid: return launch_kinds<T, kWrite | kPack | kResid>(a, s);
+    case kWrite: return launch_kinds<T, kWrite>(a, s);
+    case kResid: return launch_kinds<T, kResid>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+const void* persist_fn() {
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(k_persist<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxStepSmem) != cudaSuccess)
+      return nullptr;
+    attr_set = true;
+  }
+  return (const void*)k_persist<T>;
+}
+
+}  // namespace
+
+cudaError_t launch_step(const StepLaunch& a, int mode, cudaStream_t s) {
+  return a.dtype == 0 ? launch_step_t<double>(a, mode, s) : launch_step_t<float>(a, mode, s);
+}
+
+int persistent_max_ctas(int dtype, int smem) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  const void* fn = dtype == 0 ? persist_fn<double>() : persist_fn<float>();
+  if (!fn) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess) return 0;
+  return per_sm * sms;
+}
+
+cudaError_t launch_persistent(const PersistLaunch& a, int grid_ctas, cudaStream_t s) {
+  if (a.n_blocks <= 0 || a.n_iters <= 0) return cudaSuccess;
+  PersistLaunch args = a;
+  void* params[] = {&args};
+  const void* fn = a.dtype == 0 ? persist_fn<double>() : persist_fn<float>();
+  if (!fn) return cudaErrorInvalidValue;
+  return cudaLaunchCooperativeKernel(fn, dim3(grid_ctas), dim3(kThreads), params, a.smem, s);
+}
+
+}  // namespace jgb

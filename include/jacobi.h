@@ -328,6 +328,70 @@ int channel_pingpong(channel_t* ch, size_t bytes, int64_t round_trips, int32_t c
 
 int channel_close(channel_t* ch);
 
+/* ---- serving: continuous batching of solve requests --------------------------- */
+
+/* The paper runs one Jacobi3D problem at a time (Sec. 4.3); the server is the
+ * library's addition for many independent solves.  A background thread admits
+ * requests in arrival order while a slot and the HBM budget allow, keeps every
+ * admitted grid (states, receive slots, tables) resident on the device, and
+ * steps all of them in the same launches.  Each grid checks its FP64 relative
+ * residual every check_every iterations on the device and freezes itself when
+ * it converges (or hits its cap, or stagnates); admission and retirement happen
+ * between rounds of round_checks * check_every iterations.  A request's result
+ * does not depend on what else is running: its blocks, work items and residual
+ * summation order come from its own decomposition. */
+typedef struct serve_s serve_t;
+
+typedef struct {
+  uint64_t hbm_budget_bytes; /* admitted grids' device bytes stay below this     */
+  int32_t max_slots;         /* at most this many grids run at once (<= 1024)   */
+  int32_t dtype;             /* jacobi_dtype of every grid                       */
+  int32_t check_every;       /* iterations between convergence checks           */
+  int32_t round_checks;      /* checks per scheduling round (>= 1)              */
+  int64_t stall_checks;      /* > 0: STAGNATED after this many checks w/o a new best */
+} serve_config;
+
+typedef struct {
+  jacobi_dim3 grid;
+  jacobi_split split;
+  jacobi_init init;
+  double tol;           /* relative residual target                            */
+  int64_t max_iters;    /* cap; must be a multiple of check_every               */
+  void* out;            /* optional host buffer for the final iterate (interior
+                           layout, dtype of the server), written before the
+                           result is posted; owned by the caller             */
+} serve_request;
+
+typedef struct {
+  int32_t status;       /* jacobi_solve_status once done                        */
+  int32_t pad_;
+  int64_t iters;        /* iterations at the converged / final check            */
+  double rel;           /* relative residual of the returned iterate            */
+  int64_t t_arrive_ns;  /* host monotonic clock: submission                     */
+  int64_t t_admit_ns;   /*                       admission                      */
+  int64_t t_done_ns;    /*                       result posted                  */
+} serve_result;
+
+typedef struct {
+  int64_t submitted, admitted, completed, queued, running;
+  int64_t rounds;
+  int64_t iterations;   /* global iterations stepped                            */
+  uint64_t bytes_in_use;
+  int64_t lups;         /* lattice-site updates performed on admitted grids     */
+} serve_stats_t;
+
+/* Start a server; its thread and device tables live until serve_destroy. */
+int serve_create(const serve_config* cfg, serve_t** out);
+/* Queue a request (thread-safe, never blocks on the GPU).  JACOBI_EINVAL for
+ * bad sizes or a grid larger than the budget or the per-slot table limits. */
+int serve_submit(serve_t* s, const serve_request* req, uint64_t* ticket);
+/* JACOBI_OK with the result when done, JACOBI_EAGAIN (result->t_arrive_ns set)
+ * while pending, JACOBI_EINVAL for an unknown ticket. */
+int serve_poll(serve_t* s, uint64_t ticket, serve_result* result);
+int serve_stats(serve_t* s, serve_stats_t* out);
+/* Stop after the current round (pending requests are dropped) and free. */
+int serve_destroy(serve_t* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,27 @@ class jacobi_info_t(ctypes.Structure):
                 ("halo_bytes_per_iter", c_int64), ("workspace_bytes", c_size_t)]
 
 
+class serve_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", c_uint64), ("max_slots", c_int32), ("dtype", c_int32),
+                ("check_every", c_int32), ("round_checks", c_int32), ("stall_checks", c_int64)]
+
+
+class serve_request(ctypes.Structure):
+    _fields_ = [("grid", jacobi_dim3), ("split", jacobi_split), ("init", jacobi_init), ("tol", c_double),
+                ("max_iters", c_int64), ("out", c_void_p)]
+
+
+class serve_result(ctypes.Structure):
+    _fields_ = [("status", c_int32), ("pad_", c_int32), ("iters", c_int64), ("rel", c_double),
+                ("t_arrive_ns", c_int64), ("t_admit_ns", c_int64), ("t_done_ns", c_int64)]
+
+
+class serve_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", c_int64), ("admitted", c_int64), ("completed", c_int64), ("queued", c_int64),
+                ("running", c_int64), ("rounds", c_int64), ("iterations", c_int64), ("bytes_in_use", c_uint64),
+                ("lups", c_int64)]
+
+
 class JacobiError(RuntimeError):
     def __init__(self, code: int, func: str, msg: str):
         super().__init__(f"{func}: {msg} (code {code})")
@@ -104,6 +125,11 @@ _SIGS = {
     "channel_sync": (ctypes.c_int, [P, P]),
     "channel_pingpong": (ctypes.c_int, [P, c_size_t, c_int64, c_int32, P]),
     "channel_close": (ctypes.c_int, [P]),
+    "serve_create": (ctypes.c_int, [ctypes.POINTER(serve_config), ctypes.POINTER(P)]),
+    "serve_submit": (ctypes.c_int, [P, ctypes.POINTER(serve_request), ctypes.POINTER(c_uint64)]),
+    "serve_poll": (ctypes.c_int, [P, c_uint64, ctypes.POINTER(serve_result)]),
+    "serve_stats": (ctypes.c_int, [P, ctypes.POINTER(serve_stats_t)]),
+    "serve_destroy": (ctypes.c_int, [P]),
 }
 
 
@@ -317,6 +343,44 @@ def channel_pingpong(ch, nbytes, round_trips, ctas_per_side=1, stream=None):
 
 def channel_close(ch):
     _call("channel_close", ch)
+
+
+def serve_create(hbm_budget_bytes, max_slots, dtype="f32", check_every=100, round_checks=2, stall_checks=0) -> int:
+    cfg = serve_config(int(hbm_budget_bytes), max_slots, DTYPES[dtype], check_every, round_checks, stall_checks)
+    s = P()
+    _call("serve_create", ctypes.byref(cfg), ctypes.byref(s))
+    return s.value
+
+
+def serve_submit(s, grid, split, init=None, tol=1e-6, max_iters=20000, out=None) -> int:
+    """Queue one solve; `out` (optional) is a C-contiguous host array of the
+    server's dtype and the grid's interior shape (nz, ny, nx) that receives the
+    final iterate before the result is posted.  The caller keeps it alive."""
+    req = serve_request(jacobi_dim3(*grid), _mk_split(split), _mk_init(init), float(tol), int(max_iters),
+                        None if out is None else out.ctypes.data)
+    t = c_uint64()
+    _call("serve_submit", s, ctypes.byref(req), ctypes.byref(t))
+    return t.value
+
+
+def serve_poll(s, ticket):
+    """The serve_result when done, or None while pending."""
+    res = serve_result()
+    rc = load().serve_poll(s, ticket, ctypes.byref(res))
+    if rc == JACOBI_EAGAIN:
+        return None
+    _check(rc, "serve_poll")
+    return res
+
+
+def serve_stats(s) -> serve_stats_t:
+    out = serve_stats_t()
+    _call("serve_stats", s, ctypes.byref(out))
+    return out
+
+
+def serve_destroy(s):
+    _call("serve_destroy", s)
 
 
 # ---- convenience wrapper -----------------------------------------------------

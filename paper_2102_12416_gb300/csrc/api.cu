@@ -226,6 +226,35 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
   return JACOBI_OK;
 }
 
+void fill_block_tables(const Plan& P, char* ws, int64_t base, int32_t grid_override, BlockDev* bd, BlockGeom* geo,
+                       void** stage_tab) {
+  const int64_t nb = (int64_t)P.blocks.size();
+  for (int64_t b = 0; b < nb; ++b) {
+    const BlockHost& B = P.blocks[b];
+    BlockDev& D = bd[b];
+    memset(&D, 0, sizeof D);
+    D.u[0] = ws + B.u_off[0];
+    D.u[1] = ws + B.u_off[1];
+    for (int f = 0; f < 6; ++f) {
+      D.recv[f][0] = ws + B.recv_off[f][0];
+      D.recv[f][1] = ws + B.recv_off[f][1];
+      D.nbr[f] = B.nbr[f] >= 0 ? (int32_t)(base + B.nbr[f]) : -1;
+      if (B.nbr[f] >= 0) {
+        const BlockHost& N = P.blocks[B.nbr[f]];
+        D.send[f][0] = ws + N.recv_off[opposite(f)][0];
+        D.send[f][1] = ws + N.recv_off[opposite(f)][1];
+        if (stage_tab) stage_tab[b * 6 + f] = ws + B.stage_off[f];
+      }
+    }
+    D.nx = (int32_t)B.extent[0];
+    D.ny = (int32_t)B.extent[1];
+    D.nz = (int32_t)B.extent[2];
+    D.grid = grid_override >= 0 ? grid_override : (int32_t)B.grid;
+    D.plane_pitch = B.pitch;
+    geo[b] = BlockGeom{(int32_t)B.origin[0], (int32_t)B.origin[1], (int32_t)B.origin[2], D.grid};
+  }
+}
+
 }  // namespace jgb
 
 // ---------------------------------------------------------------------------
@@ -241,30 +270,7 @@ int upload_tables(jacobi_t* h, cudaStream_t s) {
   std::vector<BlockDev> bd(nb);
   std::vector<BlockGeom> geo(nb);
   std::vector<void*> stab(nb * 6, nullptr);
-  for (int64_t b = 0; b < nb; ++b) {
-    const BlockHost& B = P.blocks[b];
-    BlockDev& D = bd[b];
-    memset(&D, 0, sizeof D);
-    D.u[0] = h->ws + B.u_off[0];
-    D.u[1] = h->ws + B.u_off[1];
-    for (int f = 0; f < 6; ++f) {
-      D.recv[f][0] = h->ws + B.recv_off[f][0];
-      D.recv[f][1] = h->ws + B.recv_off[f][1];
-      D.nbr[f] = (int32_t)B.nbr[f];
-      if (B.nbr[f] >= 0) {
-        const BlockHost& N = P.blocks[B.nbr[f]];
-        D.send[f][0] = h->ws + N.recv_off[opposite(f)][0];
-        D.send[f][1] = h->ws + N.recv_off[opposite(f)][1];
-        stab[b * 6 + f] = h->ws + B.stage_off[f];
-      }
-    }
-    D.nx = (int32_t)B.extent[0];
-    D.ny = (int32_t)B.extent[1];
-    D.nz = (int32_t)B.extent[2];
-    D.grid = (int32_t)B.grid;
-    D.plane_pitch = B.pitch;
-    geo[b] = BlockGeom{(int32_t)B.origin[0], (int32_t)B.origin[1], (int32_t)B.origin[2], (int32_t)B.grid};
-  }
+  fill_block_tables(P, h->ws, 0, -1, bd.data(), geo.data(), stab.data());
   const int64_t ng = (int64_t)P.grids.size();
   std::vector<InitDev> ini(ng);
   std::vector<int32_t> gids(ng);
@@ -275,6 +281,8 @@ int upload_tables(jacobi_t* h, cudaStream_t s) {
     gids[g] = (int32_t)g;
     GridDev& D = h->h_grids[g];
     D.start_iter = G.start_iter;
+    D.active = 1;
+    D.pad_ = 0;
     D.item_begin = (int32_t)G.item_begin;
     D.item_end = (int32_t)G.item_end;
   }
@@ -335,7 +343,10 @@ int refresh_active(jacobi_t* h, cudaStream_t s) {
                              h->active_block_items.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   }
   // start_iter of every grid (changes when grids are frozen / re-activated)
-  for (size_t g = 0; g < P.grids.size(); ++g) h->h_grids[g].start_iter = P.grids[g].start_iter;
+  for (size_t g = 0; g < P.grids.size(); ++g) {
+    h->h_grids[g].start_iter = P.grids[g].start_iter;
+    h->h_grids[g].active = 1;  // inactive grids have no items in the launch lists
+  }
   JGB_CUDA(cudaMemcpyAsync(h->d_grids, h->h_grids, P.grids.size() * sizeof(GridDev), cudaMemcpyHostToDevice, s));
   JGB_CUDA(cudaStreamSynchronize(s));  // host mirrors are reused below
   h->tables_dirty = false;

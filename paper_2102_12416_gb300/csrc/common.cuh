@@ -56,6 +56,8 @@ struct GridDev {
   int64_t start_iter;   // global iteration at which this grid's local count was 0
   int32_t item_begin;   // partial slots [item_begin, item_end) belong to this grid
   int32_t item_end;
+  int32_t active;       // 0: frozen (step kernels leave the grid untouched)
+  int32_t pad_;
 };
 
 // Per-grid norms written by the reduction kernel.

@@ -69,6 +69,13 @@ struct Plan {
 int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* splits, jacobi_dtype dtype,
                const jacobi_init* inits, Plan* out);
 
+// Device block table entries of a plan whose workspace starts at `ws`; block
+// and neighbour ids are offset by `base`; grid_override >= 0 replaces every
+// block's grid index.  stage_tab (nullable) receives the explicit-path staging
+// buffers (6 per block).
+void fill_block_tables(const Plan& P, char* ws, int64_t base, int32_t grid_override, BlockDev* bd, BlockGeom* geo,
+                       void** stage_tab);
+
 }  // namespace jgb
 
 struct channel_s;

@@ -380,7 +380,9 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads) k_tiles(StepLaunch a) {
   const WorkItem w = a.items[blockIdx.x];
   const BlockDev& B = a.blocks[w.block];
-  const int p = (int)((a.it - a.grids[B.grid].start_iter) & 1);
+  const GridDev G = a.grids[B.grid];
+  if (!G.active) return;  // frozen grid (CTA-uniform)
+  const int p = (int)((a.it - G.start_iter) & 1);
   const double acc = tile_sweep<T, MODE>(B, p, w.x0, w.y0, w.z0, w.z1, threadIdx.x % TX, threadIdx.x / TX);
   if (MODE & kResid) {
     __shared__ double red[kThreads / 32];
@@ -416,7 +418,9 @@ __global__ void __launch_bounds__(kStreamThreads, StreamOcc<T>::min_blocks) k_st
   unsigned char* stages = smem + 128;
   const WorkItem w = a.items[blockIdx.x];
   const BlockDev& B = a.blocks[w.block];
-  const int p = (int)((a.it - a.grids[B.grid].start_iter) & 1);
+  const GridDev G = a.grids[B.grid];
+  if (!G.active) return;  // frozen grid (CTA-uniform, before any barrier)
+  const int p = (int)((a.it - G.start_iter) & 1);
   const int S = a.stages;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nx = B.nx, ny = B.ny, nz = B.nz;

@@ -45,12 +45,17 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    p.add_argument("--path", default="graph", choices=["fused", "graph", "persistent", "explicit"])
+    p.add_argument("--path", default="graph", choices=["fused", "graph", "persistent", "explicit", "auto"],
+                   help="step path; auto = the library's autotuner picks path and ring depth")
     p.add_argument("--iters", type=int, default=0, help="override the workload's iterations per step")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--cpu-iters", type=int, default=4, help="oracle iterations in the CPU sample")
     p.add_argument("--no-sweep", action="store_true", help="skip the channel ping-pong sweep")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--serve-requests", type=int, default=200,
+                   help="requests of the serving workload to run (0 = skip; 10000 = the full workload)")
+    p.add_argument("--serve-baseline", type=int, default=100,
+                   help="requests re-solved by the plain per-grid FP64 launch loop")
     return p.parse_args()
 
 
@@ -147,35 +152,55 @@ def dist_setup(args):
     return world, rank, local
 
 
-def workload_config(w, name, path):
-    grid = list(w["grid"])
-    mode, v = w["split"]
-    if mode == "count":
-        blocks = list(v)
-        shape = [-(-g // b) for g, b in zip(grid, blocks)]
+def workload_config(name, grids, splits, dtype, iters, path):
+    elem = 8 if dtype == "f64" else 4
+    points = sum(g[0] * g[1] * g[2] for g in grids)
+    cfg = {"workload": name, "dtype": dtype, "iters_per_step": iters, "path": path,
+           "l2": "inputs larger than L2 (two state copies of %.2f GB), no flush" % (points * elem / 1e9)}
+    if len(grids) == 1:
+        grid = list(grids[0])
+        mode, v = splits[0]
+        if mode == "count":
+            blocks = list(v)
+            shape = [-(-g // b) for g, b in zip(grid, blocks)]
+        else:
+            shape = list(v)
+            blocks = [-(-g // b) for g, b in zip(grid, shape)]
+        cfg.update(grid=grid, blocks=blocks, block_shape=shape)
     else:
-        shape = list(v)
-        blocks = [-(-g // b) for g, b in zip(grid, shape)]
-    return {"workload": name, "grid": grid, "blocks": blocks, "block_shape": shape, "dtype": w["dtype"],
-            "iters_per_step": w["iters"], "path": path,
-            "l2": "inputs larger than L2 (two state copies of %.2f GB each), no flush" %
-                  (grid[0] * grid[1] * grid[2] * (8 if w["dtype"] == "f64" else 4) / 1e9)}
+        cfg.update(n_grids=len(grids), points=points, block_shape=list(splits[0][1]),
+                   sides="per axis uniform over {16, 32, ..., 192}, seed 2")
+    return cfg
 
 
-def cpu_baseline(w, iters):
+def cpu_baseline(name, iters_sample):
+    """The oracle as it stands on the host cores, on a bounded sample: the first
+    `iters_sample` iterations of the workload (for a batch, of its first grids
+    up to about 64 M points)."""
     import jacobi_inputs as J
     import numpy as np
     import oracle
     oracle.build()
-    init = dict(bc=w["bc"], bc_seed=w["bc_seed"], interior=w["interior"], interior_seed=w["interior_seed"])
-    u0 = J.initial_grid(*w["grid"], dtype=np.float64 if w["dtype"] == "f64" else np.float32, **init)
-    t0 = time.perf_counter()
-    oracle.jacobi(u0, iters)
-    dt = time.perf_counter() - t0
-    n = w["grid"][0] * w["grid"][1] * w["grid"][2]
-    return {"value": n * iters / dt / 1e9, "unit": "GLUP/s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"{iters} of {w['iters']} iterations of the full {w['grid'][0]}x{w['grid'][1]}x{w['grid'][2]} "
-                      f"grid, monolithic C oracle, OpenMP over z-planes", "seconds": dt}
+    grids, _, inits, dtype, iters = J.workload_grids(name)
+    npdt = np.float64 if dtype == "f64" else np.float32
+    take, pts = [], 0
+    for g, ini in zip(grids, inits):
+        if pts and pts + g[0] * g[1] * g[2] > 64e6:
+            break
+        take.append((g, ini))
+        pts += g[0] * g[1] * g[2]
+    dt = 0.0
+    for g, ini in take:
+        u0 = J.initial_grid(*g, dtype=npdt, **ini)
+        t0 = time.perf_counter()
+        oracle.jacobi(u0, iters_sample)
+        dt += time.perf_counter() - t0
+    what = (f"{iters_sample} of {iters} iterations of the full {grids[0][0]}x{grids[0][1]}x{grids[0][2]} grid"
+            if len(grids) == 1 else f"{iters_sample} of {iters} iterations of the first {len(take)} of "
+                                    f"{len(grids)} grids ({pts / 1e6:.1f} M points)")
+    return {"value": pts * iters_sample / dt / 1e9, "unit": "GLUP/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": what + ", monolithic C oracle, OpenMP over z-planes", "seconds": dt,
+            "lups": pts * iters_sample}
 
 
 def run_reference(args):
@@ -183,25 +208,23 @@ def run_reference(args):
     if rank != 0:
         return 0
     import jacobi_inputs as J
-    w = dict(J.WORKLOADS[args.workload])
-    if args.iters > 0:
-        w["iters"] = args.iters
+    grids, splits, _, dtype, iters = J.workload_grids(args.workload)
     for _ in range(args.warmup):
-        cpu_baseline(w, args.cpu_iters)
-    vals, secs = [], []
-    cb = None
+        cpu_baseline(args.workload, args.cpu_iters)
+    secs, lups, cb = 0.0, 0, None
     for _ in range(args.steps):
-        cb = cpu_baseline(w, args.cpu_iters)
-        vals.append(cb["value"])
-        secs.append(cb["seconds"])
-    value = len(vals) * (w["grid"][0] * w["grid"][1] * w["grid"][2] * args.cpu_iters) / sum(secs) / 1e9
+        cb = cpu_baseline(args.workload, args.cpu_iters)
+        secs += cb["seconds"]
+        lups += cb["lups"]
+    value = lups / secs / 1e9
     cb = dict(cb, value=value)
     cb.pop("seconds", None)
+    cb.pop("lups", None)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": w["dtype"], "data": "synthetic",
-            "config": workload_config(w, args.workload, "cpu-oracle"),
+            "dtype": dtype, "data": "synthetic",
+            "config": workload_config(args.workload, grids, splits, dtype, iters, "cpu-oracle"),
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -232,6 +255,73 @@ def channel_sweep(jg, torch, s, stream):
     return out
 
 
+SERVE_CFG = dict(tol=1e-6, cap=20000, check_every=100, block=(32, 32, 32), budget=120 << 30, slots=128,
+                 stall_checks=20, noise_amp=1e-3)
+
+
+def serving_bench(jg, J, n_requests, n_baseline):
+    """Continuous batching of Jacobi solves (FP32 state, FP64 residual):
+    Poisson arrivals (mean 2 ms), lognormal sides clipped to [32, 256], 32^3
+    blocks, stop at 1e-6 relative residual or 20,000 iterations.  Returns
+    latency percentiles, solves/s, the served LUP rate and the same requests
+    solved one by one by the plain per-grid FP64 launch loop."""
+    c = SERVE_CFG
+    reqs = J.serving_requests(n_requests)
+    inits = [dict(bc="linear_noise", bc_seed=r["seed"], noise_amp=c["noise_amp"], interior="zero") for r in reqs]
+    split = ("shape", c["block"])
+    s = jg.serve_create(c["budget"], c["slots"], "f32", check_every=c["check_every"], round_checks=1,
+                        stall_checks=c["stall_checks"])
+    tickets = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, r in enumerate(reqs):
+            delay = r["arrival_s"] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets[i] = jg.serve_submit(s, r["grid"], split, inits[i], c["tol"], c["cap"])
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    done = {}
+    while len(done) < len(reqs):
+        for i in range(len(reqs)):
+            if i in done or tickets[i] is None:
+                continue
+            res = jg.serve_poll(s, tickets[i])
+            if res is not None:
+                done[i] = res
+        time.sleep(0.0005)
+    th.join()
+    stats = jg.serve_stats(s)
+    jg.serve_destroy(s)
+    res = [done[i] for i in range(len(reqs))]
+    lat_ms = sorted((r.t_done_ns - r.t_arrive_ns) / 1e6 for r in res)
+    span_s = (max(r.t_done_ns for r in res) - min(r.t_arrive_ns for r in res)) / 1e9
+    statuses = {k: sum(1 for r in res if r.status == v) for k, v in
+                (("converged", 0), ("max_iters", 1), ("stagnated", 2))}
+    q = lambda f: lat_ms[min(len(lat_ms) - 1, int(f * len(lat_ms)))]
+    out = {"requests": len(reqs), "solves_per_s": len(reqs) / span_s, "p50_ms": q(0.50), "p99_ms": q(0.99),
+           "offered_req_per_s": len(reqs) / max(reqs[-1]["arrival_s"], 1e-9), "wall_s": span_s,
+           "served_GLUPs": stats.lups / span_s / 1e9, "statuses": statuses, "rounds": stats.rounds,
+           "dtype": "f32 state, f64 residual", "config": dict(c, budget=int(c["budget"]))}
+    nb = min(n_baseline, len(reqs))
+    if nb > 0:
+        import torch
+        t1 = time.perf_counter()
+        base_status = {"converged": 0, "max_iters": 0, "stagnated": 0}
+        for i in range(nb):
+            with jg.Jacobi3D(reqs[i]["grid"], split, "f64", inits[i], path="fused") as h:
+                _, _, st = h.solve(c["tol"], c["cap"], c["check_every"])
+                base_status[("converged", "max_iters", "stagnated")[st[0]]] += 1
+        torch.cuda.synchronize()
+        bt = time.perf_counter() - t1
+        out["fp64_launch_loop"] = {"requests": nb, "solves_per_s": nb / bt, "wall_s": bt, "statuses": base_status,
+                                   "note": "one kernel launch per iteration, residual read on the host at each check"}
+        out["served_solves_per_s_vs_launch_loop"] = out["solves_per_s"] / (nb / bt)
+    return out
+
+
 def run_ours(args):
     world, rank, local = dist_setup(args)
     import torch
@@ -250,18 +340,19 @@ def run_ours(args):
         dist.barrier()
     jg.load()
 
-    w = dict(J.WORKLOADS[args.workload])
+    grids, splits, inits, dtype, iters = J.workload_grids(args.workload)
     if args.iters > 0:
-        w["iters"] = args.iters
-    iters = w["iters"]
-    init = dict(bc=w["bc"], bc_seed=w["bc_seed"], interior=w["interior"], interior_seed=w["interior_seed"])
-    if "noise_amp" in w:
-        init["noise_amp"] = w["noise_amp"]
+        iters = args.iters
     stream = torch.cuda.Stream()
-    n_points = w["grid"][0] * w["grid"][1] * w["grid"][2]
+    n_points = sum(g[0] * g[1] * g[2] for g in grids)
+    elem = 8 if dtype == "f64" else 4
 
     # ---- device-resident timing ------------------------------------------------
-    s = jg.Jacobi3D(w["grid"], w["split"], w["dtype"], init, path=args.path, stream=stream)
+    s = jg.Jacobi3D(grids, splits, dtype, inits, path="graph" if args.path == "auto" else args.path, stream=stream)
+    tuned = None
+    if args.path == "auto":
+        tuned = s.autotune(min(iters, 50))
+    path_used = jg.PATH_NAMES[s.info.path]
     info = s.info
     for _ in range(args.warmup):
         s.step(iters)
@@ -294,18 +385,19 @@ def run_ours(args):
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
     value = world * n_points * iters * args.steps / (total_ms * 1e-3) / 1e9
-    launches = args.steps * (iters + 2)
+    kinds = s.launch_kinds()
+    launches = args.steps * (iters * (kinds if path_used != "persistent" else 1) + kinds + 1)
 
-    # dominant kernel: the fused stencil step, one launch per iteration
+    # dominant kernel: the fused step (one launch per iteration and item kind)
     launch_s = stencil_ms * 1e-3 / (args.steps * iters)
-    elem = 8 if w["dtype"] == "f64" else 4
     peaks, peak_kind = measured_peaks()
     traffic, _ = ncu_traffic(args.workload)
-    if w["dtype"] == "f64":
+    kname = ("k_stream<%s> / k_tiles<%s> (fused stencil + face pack)" % (("double",) * 2 if dtype == "f64"
+                                                                          else ("float",) * 2))
+    if dtype == "f64":
         achieved = 6 * n_points / launch_s / 1e9
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_ADDMUL_PEAK_GFLOPS, "unit": "GFLOP/s",
-                    "frac": achieved / FP64_ADDMUL_PEAK_GFLOPS, "traffic": traffic,
-                    "kernel": "k_step<double, write|pack> (fused stencil + face pack)",
+                    "frac": achieved / FP64_ADDMUL_PEAK_GFLOPS, "traffic": traffic, "kernel": kname,
                     "peak_kind": "nominal FP64 1.25 TFLOP/s (FMA=2) -> 0.625 T add/mul per s",
                     "hbm_view": {"algorithmic_GBps": 2 * elem * n_points / launch_s / 1e9,
                                  "peak": peaks["hbm_gbs"],
@@ -314,27 +406,27 @@ def run_ours(args):
     else:
         achieved = 2 * elem * n_points / launch_s / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                    "kernel": "k_step<float, write|pack> (fused stencil + face pack)", "peak_kind": peak_kind}
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname,
+                    "peak_kind": peak_kind}
     halo = {"payload_bytes_per_iter": info.halo_bytes_per_iter,
             "GBps": info.halo_bytes_per_iter * iters * args.steps / (total_ms * 1e-3) / 1e9}
 
     # ---- end to end through the C ABI with host buffers ------------------------
-    nx, ny, nz = w["grid"]
-    npdt = torch.float64 if w["dtype"] == "f64" else torch.float32
-    u0 = J.initial_grid(nx, ny, nz, dtype="float64" if w["dtype"] == "f64" else "float32", **init)
-    h_in = torch.from_numpy(u0).pin_memory()
-    h_out = torch.empty((nz, ny, nx), dtype=npdt).pin_memory()
-    s.set_state(u0)
+    npdt = torch.float64 if dtype == "f64" else torch.float32
+    h_in = [torch.from_numpy(J.initial_grid(*g, dtype="float64" if dtype == "f64" else "float32", **ini)).pin_memory()
+            for g, ini in zip(grids, inits)]
+    h_out = [torch.empty((g[2], g[1], g[0]), dtype=npdt).pin_memory() for g in grids]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
     e2e_steps = max(args.e2e_steps, 1)
     for _ in range(e2e_steps):
-        jg.jacobi_set_state(s.h, 0, h_in.data_ptr(), False, stream)
+        for gi in range(len(grids)):
+            jg.jacobi_set_state(s.h, gi, h_in[gi].data_ptr(), False, stream)
         s.step(iters)
         s.residual()
-        jg.jacobi_copy_out(s.h, 0, h_out.data_ptr(), False, jg.JACOBI_LAYOUT_INTERIOR, stream)
+        for gi in range(len(grids)):
+            jg.jacobi_copy_out(s.h, gi, h_out[gi].data_ptr(), False, jg.JACOBI_LAYOUT_INTERIOR, stream)
     e1.record(stream)
     e1.synchronize()
     e2e_ms = e0.elapsed_time(e1)
@@ -343,28 +435,35 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
     e2e = {"value": world * n_points * iters * e2e_steps / (e2e_ms * 1e-3) / 1e9, "unit": "GLUP/s",
-           "h2d_bytes_per_step": h_in.numel() * h_in.element_size(),
-           "d2h_bytes_per_step": h_out.numel() * h_out.element_size() + 8 * 4, "steps": e2e_steps}
+           "h2d_bytes_per_step": sum(x.numel() * x.element_size() for x in h_in),
+           "d2h_bytes_per_step": sum(x.numel() * x.element_size() for x in h_out) + 16 * len(grids),
+           "steps": e2e_steps}
 
     sweep = None
     if not args.no_sweep and rank == 0:
         sweep = channel_sweep(jg, torch, s, stream)
     s.close()
+    del h_in, h_out
+
+    serving = None
+    if rank == 0 and args.serve_requests > 0:
+        serving = serving_bench(jg, J, args.serve_requests, args.serve_baseline)
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cb = cpu_baseline(w, args.cpu_iters)
+        cb = cpu_baseline(args.workload, args.cpu_iters)
         cb.pop("seconds", None)
+        cb.pop("lups", None)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": w["dtype"], "data": "synthetic",
-                "config": dict(workload_config(w, args.workload, args.path),
-                               parallelism=f"replicas{world}" if world > 1 else "single-gpu"),
+                "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+                "config": dict(workload_config(args.workload, grids, splits, dtype, iters, path_used),
+                               parallelism=f"replicas{world}" if world > 1 else "single-gpu", autotune=tuned),
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "halo": halo, "final_rel_residual": rel[0] if rel else None,
-                "channel_pingpong": sweep}
+                "channel_pingpong": sweep, "serving": serving}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

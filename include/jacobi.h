@@ -147,7 +147,18 @@ typedef struct {
   int32_t path;
   int64_t halo_bytes_per_iter; /* face payload moved per iteration (bytes) */
   size_t workspace_bytes;
+  int32_t stages;        /* ring depth of the plane-streaming kernels          */
+  int32_t item_kinds;    /* kernel variants launched per iteration (fused paths) */
 } jacobi_info_t;
+
+/* Outcome of jacobi_autotune. */
+typedef struct {
+  int32_t path;          /* chosen jacobi_path                                  */
+  int32_t stages;        /* chosen ring depth                                   */
+  double ms_per_iter;    /* measured time per iteration of the chosen config    */
+  int32_t n_tried;       /* candidates timed (0 when taken from the cache)      */
+  int32_t from_cache;
+} jacobi_tune_result;
 
 /* ---- errors -------------------------------------------------------------- */
 const char* jacobi_strerror(int code);
@@ -199,6 +210,16 @@ int jacobi_block(const jacobi_t* h, int64_t block, jacobi_block_info* out);
 /* Select the step path (jacobi_path).  PERSISTENT fails with JACOBI_EINVAL at
  * the next step if the blocks cannot all be co-resident on the GPU. */
 int jacobi_set_path(jacobi_t* h, int32_t path);
+
+/* Autotuner (the library's addition): times every candidate step
+ * configuration -- path FUSED/GRAPH/PERSISTENT x ring depth 3..6 of the
+ * plane-streaming kernels, where it fits shared memory -- for iters_per_trial
+ * iterations on a scratch handle with the same grids, splits and dtype (the
+ * handle's own state is untouched), then applies the fastest to `h`.  All
+ * candidates give bit-identical iterates.  When the environment variable
+ * JACOBI_TUNE_CACHE names a file, results are looked up there by a signature
+ * of the geometry and appended after a search.  Synchronises the stream. */
+int jacobi_autotune(jacobi_t* h, int64_t iters_per_trial, void* stream, jacobi_tune_result* out);
 
 /* ---- state transfer ---------------------------------------------------------- */
 

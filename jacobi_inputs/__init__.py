@@ -147,6 +147,31 @@ WORKLOADS = {
 }
 
 
+# Batched workloads: `n_grids` independent grids with sides drawn by
+# batched_sides(), each split into blocks of `block` (partial edge blocks).
+BATCHED = {
+    "jacobi3d-batched256-fp32": dict(n_grids=256, sides_seed=2, block=(32, 32, 32), dtype="f32", bc="uniform",
+                                     interior="zero", iters=500),
+    "jacobi3d-batched256-fp64": dict(n_grids=256, sides_seed=2, block=(32, 32, 32), dtype="f64", bc="uniform",
+                                     interior="zero", iters=500),
+}
+
+
+def workload_grids(name: str):
+    """(grids, splits, inits, dtype, iters) of a named workload (single or batched)."""
+    if name in WORKLOADS:
+        w = WORKLOADS[name]
+        init = dict(bc=w["bc"], bc_seed=w["bc_seed"], interior=w["interior"], interior_seed=w["interior_seed"])
+        if "noise_amp" in w:
+            init["noise_amp"] = w["noise_amp"]
+        return [w["grid"]], [w["split"]], [init], w["dtype"], w["iters"]
+    b = BATCHED[name]
+    sides = batched_sides(b["n_grids"], b["sides_seed"])
+    inits = [dict(bc=b["bc"], bc_seed=batched_seed(g, b["sides_seed"]), interior=b["interior"])
+             for g in range(b["n_grids"])]
+    return sides, [("shape", b["block"])] * b["n_grids"], inits, b["dtype"], b["iters"]
+
+
 def batched_sides(n_grids: int = 256, seed: int = 2):
     """Per-grid (nx, ny, nz), each side uniform over {16, 32, ..., 192}."""
     u = u01(seed, np.arange(3 * n_grids, dtype=np.uint64)).reshape(n_grids, 3)

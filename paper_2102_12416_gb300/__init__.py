@@ -36,6 +36,7 @@ FACES = ("xm", "xp", "ym", "yp", "zm", "zp")
 
 PATHS = {"fused": JACOBI_PATH_FUSED, "explicit": JACOBI_PATH_EXPLICIT,
          "persistent": JACOBI_PATH_PERSISTENT, "graph": JACOBI_PATH_GRAPH}
+PATH_NAMES = {v: k for k, v in PATHS.items()}
 DTYPES = {"f64": JACOBI_F64, "f32": JACOBI_F32}
 NP_DTYPES = {JACOBI_F64: np.float64, JACOBI_F32: np.float32}
 BCS = {"linear": JACOBI_BC_LINEAR, "linear_noise": JACOBI_BC_LINEAR_NOISE, "uniform": JACOBI_BC_UNIFORM}
@@ -63,7 +64,13 @@ class jacobi_block_info(ctypes.Structure):
 class jacobi_info_t(ctypes.Structure):
     _fields_ = [("n_grids", c_int64), ("n_blocks", c_int64), ("n_points", c_int64),
                 ("iteration", c_int64), ("dtype", c_int32), ("path", c_int32),
-                ("halo_bytes_per_iter", c_int64), ("workspace_bytes", c_size_t)]
+                ("halo_bytes_per_iter", c_int64), ("workspace_bytes", c_size_t), ("stages", c_int32),
+                ("item_kinds", c_int32)]
+
+
+class jacobi_tune_result(ctypes.Structure):
+    _fields_ = [("path", c_int32), ("stages", c_int32), ("ms_per_iter", c_double), ("n_tried", c_int32),
+                ("from_cache", c_int32)]
 
 
 class serve_config(ctypes.Structure):
@@ -115,6 +122,7 @@ _SIGS = {
     "jacobi_residual": (ctypes.c_int, [P, P, P, P]),
     "jacobi_solve": (ctypes.c_int, [P, c_double, c_int64, c_int64, c_int64, P, P, P, P]),
     "jacobi_sync": (ctypes.c_int, [P, P]),
+    "jacobi_autotune": (ctypes.c_int, [P, c_int64, P, ctypes.POINTER(jacobi_tune_result)]),
     "jacobi_read_face": (ctypes.c_int, [P, c_int64, c_int32, P, P]),
     "jacobi_debug_drop_block": (ctypes.c_int, [P, c_int64]),
     "jacobi_residual_noalloc": (ctypes.c_int, [P, jacobi_dim3, ctypes.c_int, P, P]),
@@ -291,6 +299,12 @@ def jacobi_solve(h, n_grids, tol, max_iters, check_every, stall_checks=0, stream
     return list(it), list(rel), list(st)
 
 
+def jacobi_autotune(h, iters_per_trial, stream=None) -> jacobi_tune_result:
+    out = jacobi_tune_result()
+    _call("jacobi_autotune", h, iters_per_trial, _stream(stream), ctypes.byref(out))
+    return out
+
+
 def jacobi_sync(h, stream=None):
     _call("jacobi_sync", h, _stream(stream))
 
@@ -431,6 +445,14 @@ class Jacobi3D:
 
     def sync(self):
         jacobi_sync(self.h, self.stream)
+
+    def autotune(self, iters_per_trial=50) -> dict:
+        r = jacobi_autotune(self.h, iters_per_trial, self.stream)
+        return {"path": PATH_NAMES[r.path], "stages": r.stages, "ms_per_iter": r.ms_per_iter,
+                "n_tried": r.n_tried, "from_cache": bool(r.from_cache)}
+
+    def launch_kinds(self) -> int:
+        return max(1, self.info.item_kinds)
 
     def residual(self):
         return jacobi_residual(self.h, len(self.grids), self.stream)

@@ -304,6 +304,10 @@ int upload_tables(jacobi_t* h, cudaStream_t s) {
 // Rebuild the active item / block lists from the grids' active flags.
 int refresh_active(jacobi_t* h, cudaStream_t s) {
   if (!h->tables_dirty) return JACOBI_OK;
+  if (h->graph) {  // the captured launches bake in the old lists
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
   const Plan& P = h->plan;
   h->active_items.clear();
   h->active_blocks.clear();
@@ -739,6 +743,136 @@ int jacobi_info(const jacobi_t* h, jacobi_info_t* out) {
   out->path = h->path;
   out->halo_bytes_per_iter = h->plan.halo_elems * (int64_t)h->plan.elem;
   out->workspace_bytes = h->plan.bytes;
+  out->stages = h->stages;
+  int kinds = 0;
+  for (int k = 0; k < kItemKinds; ++k) kinds += h->kind_off[k + 1] > h->kind_off[k] ? 1 : 0;
+  out->item_kinds = kinds;
+  return JACOBI_OK;
+}
+
+// ---- autotuner ------------------------------------------------------------------
+namespace {
+
+uint64_t geometry_signature(const Plan& P) {
+  uint64_t x = 1469598103934665603ull;  // FNV-1a
+  auto mix = [&](int64_t v) {
+    for (int b = 0; b < 8; ++b) {
+      x ^= (uint64_t)((v >> (8 * b)) & 0xff);
+      x *= 1099511628211ull;
+    }
+  };
+  mix(P.dtype);
+  mix((int64_t)P.grids.size());
+  for (const GridHost& G : P.grids) {
+    mix(G.dims.nx); mix(G.dims.ny); mix(G.dims.nz);
+    mix(G.split.mode); mix(G.split.x); mix(G.split.y); mix(G.split.z);
+  }
+  return x;
+}
+
+bool cache_lookup(uint64_t key, int32_t* path, int32_t* stages, double* ms) {
+  const char* f = getenv("JACOBI_TUNE_CACHE");
+  if (!f || !*f) return false;
+  FILE* fp = fopen(f, "r");
+  if (!fp) return false;
+  unsigned long long k;
+  int p, st;
+  double t;
+  bool found = false;
+  while (fscanf(fp, "%llx %d %d %lf", &k, &p, &st, &t) == 4)
+    if (k == key) {
+      *path = p; *stages = st; *ms = t;
+      found = true;  // the last entry wins
+    }
+  fclose(fp);
+  return found;
+}
+
+void cache_store(uint64_t key, int32_t path, int32_t stages, double ms) {
+  const char* f = getenv("JACOBI_TUNE_CACHE");
+  if (!f || !*f) return;
+  FILE* fp = fopen(f, "a");
+  if (!fp) return;
+  fprintf(fp, "%016llx %d %d %.6f\n", (unsigned long long)key, path, stages, ms);
+  fclose(fp);
+}
+
+}  // namespace
+
+extern "C" int jacobi_autotune(jacobi_t* h, int64_t iters_per_trial, void* stream, jacobi_tune_result* out) {
+  if (!h || iters_per_trial < 1) return set_error(JACOBI_EINVAL, "bad arguments to jacobi_autotune");
+  const cudaStream_t s = S(stream);
+  const Plan& P = h->plan;
+  const uint64_t key = geometry_signature(P);
+  jacobi_tune_result r{};
+  if (cache_lookup(key, &r.path, &r.stages, &r.ms_per_iter)) {
+    r.from_cache = 1;
+  } else {
+    std::vector<jacobi_dim3> grids;
+    std::vector<jacobi_split> splits;
+    std::vector<jacobi_init> inits;
+    for (const GridHost& G : P.grids) {
+      grids.push_back(G.dims);
+      splits.push_back(G.split);
+      inits.push_back(G.init);
+    }
+    jacobi_t* t = nullptr;
+    int rc = jacobi_create_batch((int64_t)grids.size(), grids.data(), splits.data(), (jacobi_dtype)P.dtype,
+                                 inits.data(), nullptr, 0, stream, &t);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = INFINITY;
+    const int32_t paths[3] = {JACOBI_PATH_GRAPH, JACOBI_PATH_PERSISTENT, JACOBI_PATH_FUSED};
+    for (int32_t path : paths) {
+      for (int32_t st = 3; st <= 6; ++st) {
+        if (128 + st * (int64_t)P.max_stage > kMaxStepSmem) continue;
+        if (P.max_stage == 0 && st != 3) continue;  // no plane-streamed blocks: the depth is irrelevant
+        t->stages = st;
+        t->path = path;
+        t->tables_dirty = true;
+        rc = do_step(t, std::max<int64_t>(iters_per_trial / 4, 2), s);  // warm-up (graph capture etc.)
+        if (!rc && cudaEventRecord(e0, s) != cudaSuccess) rc = JACOBI_ECUDA;
+        if (!rc) rc = do_step(t, iters_per_trial, s);
+        if (!rc && cudaEventRecord(e1, s) != cudaSuccess) rc = JACOBI_ECUDA;
+        if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = JACOBI_ECUDA;
+        if (!rc) rc = check_err_word(t, s);
+        if (rc) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          jacobi_destroy(t);
+          return rc;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / (double)iters_per_trial;
+        r.n_tried += 1;
+        if (per < best) {
+          best = per;
+          r.path = path;
+          r.stages = st;
+          r.ms_per_iter = per;
+        }
+        if (t->graph) {
+          cudaGraphExecDestroy(t->graph);
+          t->graph = nullptr;
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    jacobi_destroy(t);
+    cache_store(key, r.path, r.stages, r.ms_per_iter);
+  }
+  h->path = r.path;
+  h->stages = r.stages;
+  h->tables_dirty = true;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  if (out) *out = r;
   return JACOBI_OK;
 }
 

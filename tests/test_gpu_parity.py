@@ -268,6 +268,52 @@ def test_config2_eigenmode_closed_form():
     assert np.max(np.abs(got - want)) <= 1e-11 * np.max(np.abs(want))
 
 
+# ---- the batched workload: 256 grids, sides in {16..192}, 32^3 blocks -----------
+
+def _batched(name):
+    return J.workload_grids(name)
+
+
+@pytest.mark.parametrize("name", ["jacobi3d-batched256-fp32", "jacobi3d-batched256-fp64"])
+def test_batched_full_size(oracle_mod, name):
+    """All 256 grids stepped together for the workload's 500 iterations: the
+    graph and persistent paths agree bit for bit on every grid, and the three
+    smallest grids (which the oracle finishes in seconds) match the oracle."""
+    grids, splits, inits, dtype, iters = _batched(name)
+    npdt = np.float64 if dtype == "f64" else np.float32
+    small = sorted(range(len(grids)), key=lambda g: grids[g][0] * grids[g][1] * grids[g][2])[:3]
+    outs = {}
+    for path in ("graph", "persistent"):
+        with jg.Jacobi3D(grids, splits, dtype, inits, path=path) as s:
+            s.step(iters)
+            s.sync()
+            outs[path] = [s.copy_out(g) for g in range(len(grids))]
+    for g in range(len(grids)):
+        assert np.array_equal(outs["graph"][g], outs["persistent"][g]), g
+    for g in small:
+        want = oracle_mod.jacobi(J.initial_grid(*grids[g], dtype=npdt, **inits[g]), iters)
+        assert np.array_equal(outs["graph"][g], J.interior_of(want)), g
+
+
+def test_autotune_keeps_results(tmp_path, monkeypatch, oracle_mod):
+    monkeypatch.setenv("JACOBI_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    grids, splits, inits, dtype, _ = _batched("jacobi3d-batched256-fp32")
+    grids, splits, inits = grids[:12], splits[:12], inits[:12]
+    with jg.Jacobi3D(grids, splits, dtype, inits) as s:
+        r = s.autotune(8)
+        assert r["n_tried"] >= 3 and not r["from_cache"] and r["ms_per_iter"] > 0
+        assert jg.PATH_NAMES[s.info.path] == r["path"] and s.info.stages == r["stages"]
+        s.step(17)
+        s.sync()
+        tuned = [s.copy_out(g) for g in range(len(grids))]
+    with jg.Jacobi3D(grids, splits, dtype, inits) as s:
+        r2 = s.autotune(8)
+        assert r2["from_cache"] and (r2["path"], r2["stages"]) == (r["path"], r["stages"])
+    for g in (0, 5, 11):
+        want = oracle_mod.jacobi(J.initial_grid(*grids[g], dtype=np.float32, **inits[g]), 17)
+        assert np.array_equal(tuned[g], J.interior_of(want))
+
+
 # ---- failure detection: bounded waits, no hang ----------------------------------
 
 def test_persistent_wait_times_out(monkeypatch):

@@ -75,7 +75,7 @@ static int64_t face_elems_host(const BlockHost& b, int f) {
 }
 
 int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* splits, jacobi_dtype dtype,
-               const jacobi_init* inits, Plan* P) {
+               const jacobi_init* inits, Plan* P, int64_t target_items) {
   if (n_grids < 1 || !grids || !splits) return set_error(JACOBI_EINVAL, "need at least one grid");
   if (dtype != JACOBI_F64 && dtype != JACOBI_F32) return set_error(JACOBI_EINVAL, "bad dtype %d", (int)dtype);
   *P = Plan();
@@ -133,27 +133,32 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
         }
     G.block_end = (int64_t)P->blocks.size();
     if (G.block_end > (1ll << 30)) return set_error(JACOBI_EINVAL, "too many blocks");
-    // Work items of this grid.  Blocks that fit the plane-streaming path get
-    // one item per z-chunk; the others one item per TX x TY tile and z-chunk.
-    // The chunk depends only on this grid, so a grid's items (and its
-    // residual summation order) are the same alone or in a batch.
-    int64_t units = 0, maxz = 0;
-    std::vector<int> rows(G.block_end - G.block_begin);
-    for (int64_t b = G.block_begin; b < G.block_end; ++b) {
-      const BlockHost& B = P->blocks[b];
-      uint32_t sb = 0;
-      const int ry = stream_rows(B.extent[0], B.extent[1], P->elem, &sb);
-      rows[b - G.block_begin] = ry;
-      if (ry) P->max_stage = std::max(P->max_stage, sb);
-      units += ry ? 1 : ((B.extent[0] + TX - 1) / TX) * ((B.extent[1] + TY - 1) / TY);
-      maxz = std::max(maxz, B.extent[2]);
-    }
-    int64_t zc = maxz;
-    while (zc > 16 && units * ((maxz + zc - 1) / zc) < 2048) zc = (zc + 1) / 2;
+    P->n_points += d.nx * d.ny * d.nz;
+    P->grids.push_back(G);
+  }
+  // Work items.  Blocks that fit the plane-streaming path get one item per
+  // z-chunk; the others one item per TX x TY tile and z-chunk.  The chunk is
+  // the largest power-of-two fraction of the tallest block that still gives
+  // at least `target_items` items (or 2 planes), so small problems still
+  // spread over many CTAs while large ones stream whole blocks.
+  std::vector<int> rows(P->blocks.size());
+  int64_t units = 0, maxz = 0;
+  for (size_t b = 0; b < P->blocks.size(); ++b) {
+    const BlockHost& B = P->blocks[b];
+    uint32_t sb = 0;
+    const int ry = stream_rows(B.extent[0], B.extent[1], P->elem, &sb);
+    rows[b] = ry;
+    if (ry) P->max_stage = std::max(P->max_stage, sb);
+    units += ry ? 1 : ((B.extent[0] + TX - 1) / TX) * ((B.extent[1] + TY - 1) / TY);
+    maxz = std::max(maxz, B.extent[2]);
+  }
+  int64_t zc = maxz;
+  while (zc > 2 && units * ((maxz + zc - 1) / zc) < target_items) zc = (zc + 1) / 2;
+  for (GridHost& G : P->grids) {
     G.item_begin = (int64_t)P->items.size();
     for (int64_t b = G.block_begin; b < G.block_end; ++b) {
       BlockHost& B = P->blocks[b];
-      const int ry = rows[b - G.block_begin];
+      const int ry = rows[b];
       B.item_begin = (int64_t)P->items.size();
       for (int64_t z0 = 0; z0 < B.extent[2]; z0 += zc) {
         WorkItem w;
@@ -178,10 +183,8 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
       B.item_end = (int64_t)P->items.size();
     }
     G.item_end = (int64_t)P->items.size();
-    if (G.item_end > (1ll << 30)) return set_error(JACOBI_EINVAL, "too many work items");
-    P->n_points += d.nx * d.ny * d.nz;
-    P->grids.push_back(G);
   }
+  if ((int64_t)P->items.size() > (1ll << 30)) return set_error(JACOBI_EINVAL, "too many work items");
   const int64_t nb = (int64_t)P->blocks.size(), ni = (int64_t)P->items.size(), ng = n_grids;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, A); return o; };

@@ -202,7 +202,9 @@ def test_solve_cap_and_stagnation(oracle_mod):
 
 
 def test_batched_solve_alone_equals_mix(oracle_mod):
-    """Each grid's result in a batch is bit-identical to solving it alone."""
+    """Each grid's state in a batch is bit-identical to solving it alone, with
+    the same iteration count; the residual may differ in its last bits because
+    a handle splits blocks into work items according to its total size."""
     grids = [(24, 16, 40), (16, 16, 16), (48, 32, 16)]
     inits = [dict(bc="uniform", bc_seed=(2 << 32) | g, interior="zero") for g in range(3)]
     splits = [("shape", (16, 16, 16))] * 3
@@ -213,7 +215,8 @@ def test_batched_solve_alone_equals_mix(oracle_mod):
         with jg.Jacobi3D([grids[g]], [splits[g]], "f64", [inits[g]]) as s1:
             it1, rel1, st1 = s1.solve(1e-7, 20000, 10)
             alone = s1.copy_out()
-        assert (it1[0], st1[0], rel1[0]) == (its[g], sts[g], rels[g])
+        assert (it1[0], st1[0]) == (its[g], sts[g])
+        assert abs(rel1[0] - rels[g]) <= RES_TOL * rels[g]
         assert np.array_equal(alone, mix[g])
         _, k, _, _ = oracle_mod.solve(J.initial_grid(*grids[g], **inits[g]), 1e-7, 20000, 10)
         assert k == its[g]

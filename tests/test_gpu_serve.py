@@ -71,7 +71,10 @@ def test_served_equals_standalone_and_oracle_f64(oracle_mod):
         with jg.Jacobi3D(g, sp, "f64", ini) as h:
             it, rel, st = h.solve(tol, cap, check)
             alone = h.copy_out()
-        assert (r.iters, r.status, r.rel) == (it[0], st[0], rel[0])
+        # a handle splits its blocks into more work items than the server does,
+        # so only the residual's summation order differs
+        assert (r.iters, r.status) == (it[0], st[0])
+        assert abs(r.rel - rel[0]) <= RES_TOL * rel[0]
         assert np.array_equal(o, alone)
         want, k, orel, ost = oracle_mod.solve(J.initial_grid(*g, **ini), tol, cap, check)
         assert (r.iters, r.status) == (k, ost)

@@ -149,6 +149,9 @@ typedef struct {
   size_t workspace_bytes;
   int32_t stages;        /* ring depth of the plane-streaming kernels          */
   int32_t item_kinds;    /* kernel variants launched per iteration (fused paths) */
+  int32_t fp64_int_adds; /* FP64 adds per update run on the integer pipe (0 or 3)
+                            for grids inside the integer adder's domain         */
+  int32_t pad_;
 } jacobi_info_t;
 
 /* Outcome of jacobi_autotune. */
@@ -270,6 +273,23 @@ int jacobi_sync(jacobi_t* h, void* stream);
  * dtype).  After a step this is the neighbour's packed boundary plane (or the
  * Dirichlet boundary).  Synchronises the stream. */
 int jacobi_read_face(jacobi_t* h, int64_t block, int32_t face, void* dst, void* stream);
+
+/* Test support for the FP64 stencil's integer-pipe adder: out[i] = a[i] + b[i]
+ * (device arrays of n doubles) computed by the integer-pipe routine the FP64
+ * step kernels use for the neighbour pair sums.  For a[i], b[i] >= 0 with
+ * exponent field < 2040 the result is the IEEE-754 round-to-nearest-even sum
+ * bit for bit; other inputs give unspecified values (the step kernels never
+ * pass them: a device check keeps such grids on the FP64 pipe).  Setting the
+ * environment variable JACOBI_FP64_EMU=0 before jacobi_create keeps every
+ * FP64 add on the FP64 pipe.  Asynchronous. */
+int jacobi_selftest_dadd(const double* a, const double* b, int64_t n, double* out, void* stream);
+
+/* Measured issue rates of this GPU's two add pipes (for rooflines): FP64 adds
+ * per second on the FP64 pipe, and FP64 adds per second through the
+ * integer-pipe routine of jacobi_selftest_dadd; each from one timed launch of
+ * 8 independent add chains per thread.  Synchronises the stream; allocates a
+ * small scratch buffer. */
+int jacobi_pipe_rates(double* fp64_adds_per_s, double* int_adds_per_s, void* stream);
 
 /* Host-side fault injection for tests: the next persistent steps leave block
  * `block` out of the launch (its sends never happen), so its neighbours'

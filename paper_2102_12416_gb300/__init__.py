@@ -65,7 +65,7 @@ class jacobi_info_t(ctypes.Structure):
     _fields_ = [("n_grids", c_int64), ("n_blocks", c_int64), ("n_points", c_int64),
                 ("iteration", c_int64), ("dtype", c_int32), ("path", c_int32),
                 ("halo_bytes_per_iter", c_int64), ("workspace_bytes", c_size_t), ("stages", c_int32),
-                ("item_kinds", c_int32)]
+                ("item_kinds", c_int32), ("fp64_int_adds", c_int32), ("pad_", c_int32)]
 
 
 class jacobi_tune_result(ctypes.Structure):
@@ -125,6 +125,8 @@ _SIGS = {
     "jacobi_autotune": (ctypes.c_int, [P, c_int64, P, ctypes.POINTER(jacobi_tune_result)]),
     "jacobi_read_face": (ctypes.c_int, [P, c_int64, c_int32, P, P]),
     "jacobi_debug_drop_block": (ctypes.c_int, [P, c_int64]),
+    "jacobi_selftest_dadd": (ctypes.c_int, [P, P, c_int64, P, P]),
+    "jacobi_pipe_rates": (ctypes.c_int, [ctypes.POINTER(c_double), ctypes.POINTER(c_double), P]),
     "jacobi_residual_noalloc": (ctypes.c_int, [P, jacobi_dim3, ctypes.c_int, P, P]),
     "channel_open": (ctypes.c_int, [P, c_uint32, c_int64, c_int64, c_size_t, ctypes.POINTER(P)]),
     "channel_send": (ctypes.c_int, [P, c_int64, P, c_size_t, P]),
@@ -311,6 +313,17 @@ def jacobi_sync(h, stream=None):
 
 def jacobi_read_face(h, block, face, dst: np.ndarray, stream=None):
     _call("jacobi_read_face", h, block, face, dst.ctypes.data, _stream(stream))
+
+
+def jacobi_selftest_dadd(a_dev, b_dev, n, out_dev, stream=None):
+    _call("jacobi_selftest_dadd", int(a_dev), int(b_dev), n, int(out_dev), _stream(stream))
+
+
+def jacobi_pipe_rates(stream=None):
+    """(FP64-pipe adds/s, integer-pipe FP64 adds/s) measured on the current GPU."""
+    a, b = c_double(), c_double()
+    _call("jacobi_pipe_rates", ctypes.byref(a), ctypes.byref(b), _stream(stream))
+    return a.value, b.value
 
 
 def jacobi_debug_drop_block(h, block):

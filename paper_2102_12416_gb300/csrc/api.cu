@@ -50,22 +50,35 @@ static int axis_split(int64_t n, int32_t mode, int64_t param, std::vector<std::p
 }
 
 // Rows per thread for the plane-streaming path, or 0 when the block shape does
-// not fit it: rows must split into 16-byte vectors (which also keeps every
-// bulk copy 16-byte aligned), one CTA of kThreads threads must cover a plane
-// with at most 8 rows per thread, and a ring stage must fit shared memory.
-static int stream_rows(int64_t nx, int64_t ny, size_t elem, uint32_t* stage_bytes) {
+// not fit it.  Rows must split into 16-byte vectors (which also keeps every
+// bulk copy 16-byte aligned); one CTA of kThreads threads covers a window of
+// `chunk` rows (a multiple of both the rows per thread and the vector width),
+// so a plane is split into ceil(ny / chunk) windows; a ring stage of a window
+// must fit shared memory four times over.
+static int stream_rows(int64_t nx, int64_t ny, size_t elem, uint32_t* stage_bytes, int64_t* chunk) {
   const int64_t vec = 16 / (int64_t)elem;
   if (nx % vec || ny % vec) return 0;
   const int64_t txv = nx / vec;
   if (txv > kThreads) return 0;
-  const uint64_t stage = ((uint64_t)(nx * ny + 2 * (nx + ny)) * elem + 127) / 128 * 128;
+  const int64_t tpr = kThreads / txv;
+  int ry = 0;
+  int64_t ch = 0;
+  for (int r = 1; r <= 4; r *= 2) {
+    if (ny % r) break;
+    const int64_t L = std::max<int64_t>(r, vec);
+    const int64_t c = tpr * r / L * L;
+    if (c <= 0) continue;
+    ry = r;
+    ch = c;
+    if (c >= ny) break;
+  }
+  if (!ry) return 0;
+  ch = std::min(ch, ny);
+  const uint64_t stage = ((uint64_t)((ch + 2) * nx + 2 * ch + 2 * nx) * elem + 127) / 128 * 128;
   if (128 + 4 * stage > (uint64_t)kMaxStepSmem) return 0;
-  for (int ry = 1; ry <= 8; ry *= 2)
-    if (ny % ry == 0 && txv * (ny / ry) <= kThreads) {
-      *stage_bytes = (uint32_t)stage;
-      return ry;
-    }
-  return 0;
+  *stage_bytes = (uint32_t)stage;
+  *chunk = ch;
+  return ry;
 }
 
 static int64_t face_elems_host(const BlockHost& b, int f) {
@@ -142,14 +155,17 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
   // at least `target_items` items (or 2 planes), so small problems still
   // spread over many CTAs while large ones stream whole blocks.
   std::vector<int> rows(P->blocks.size());
+  std::vector<int64_t> chunks(P->blocks.size());
   int64_t units = 0, maxz = 0;
   for (size_t b = 0; b < P->blocks.size(); ++b) {
     const BlockHost& B = P->blocks[b];
     uint32_t sb = 0;
-    const int ry = stream_rows(B.extent[0], B.extent[1], P->elem, &sb);
+    int64_t ch = 0;
+    const int ry = stream_rows(B.extent[0], B.extent[1], P->elem, &sb, &ch);
     rows[b] = ry;
+    chunks[b] = ch;
     if (ry) P->max_stage = std::max(P->max_stage, sb);
-    units += ry ? 1 : ((B.extent[0] + TX - 1) / TX) * ((B.extent[1] + TY - 1) / TY);
+    units += ry ? (B.extent[1] + ch - 1) / ch : ((B.extent[0] + TX - 1) / TX) * ((B.extent[1] + TY - 1) / TY);
     maxz = std::max(maxz, B.extent[2]);
   }
   int64_t zc = maxz;
@@ -165,11 +181,16 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
         w.block = (int32_t)b;
         w.z0 = (int16_t)z0;
         w.z1 = (int16_t)std::min(B.extent[2], z0 + zc);
+        w.ya = w.yb = 0;
         if (ry) {
-          w.slot = (int32_t)P->items.size();
-          w.x0 = -1;
-          w.y0 = (int16_t)ry;
-          P->items.push_back(w);
+          for (int64_t ya = 0; ya < B.extent[1]; ya += chunks[b]) {
+            w.slot = (int32_t)P->items.size();
+            w.x0 = -1;
+            w.y0 = (int16_t)ry;
+            w.ya = (int16_t)ya;
+            w.yb = (int16_t)std::min(B.extent[1], ya + chunks[b]);
+            P->items.push_back(w);
+          }
           continue;
         }
         for (int64_t y0 = 0; y0 < B.extent[1]; y0 += TY)
@@ -376,6 +397,8 @@ StepLaunch step_args(jacobi_t* h, int64_t it, bool all_items) {
   a.smem = 128 + h->stages * (int32_t)h->plan.max_stage;
   a.err = h->d_err;
   a.wait_ns = h->wait_ns;
+  a.norms = h->d_norms;
+  a.emu = h->fp64_emu;
   return a;
 }
 
@@ -462,6 +485,9 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
   a.dtype = h->plan.dtype;
   a.stages = h->stages;
   a.smem = smem;
+  a.norms = h->d_norms;
+  a.emu = h->fp64_emu;
+  a.pad_ = 0;
   const int ctas = std::min(maxc, a.n_blocks);
   JGB_CUDA(launch_persistent(a, ctas, s));
   return JACOBI_OK;
@@ -530,6 +556,9 @@ int residual_only(jacobi_t* h, cudaStream_t s) {
 
 int compute_bnorm(jacobi_t* h, cudaStream_t s) {
   StepLaunch a = step_args(h, h->iter, true);
+  if (h->plan.dtype == JACOBI_F64)
+    JGB_CUDA(launch_emu_check(h->d_blocks, (int32_t)h->plan.blocks.size(), h->d_grids, h->d_norms, h->d_gids,
+                              (int32_t)h->plan.grids.size(), h->iter, s));
   JGB_CUDA(launch_bnorm(a, s));
   JGB_CUDA(launch_reduce(h->d_grids, h->d_norms, h->d_gids, (int32_t)h->plan.grids.size(), h->d_partials, 1, s));
   return JACOBI_OK;
@@ -696,10 +725,10 @@ int jacobi_create_batch(int64_t n_grids, const jacobi_dim3* grids, const jacobi_
     const double ms = atof(w);
     if (ms > 0) h->wait_ns = (uint64_t)(ms * 1e6);
   }
-  // Ring depth of the plane-streaming path: FP32 is bandwidth-bound and wants
-  // two planes in flight per CTA; FP64 is bound by the FP64 pipe and prefers
-  // a shallower ring so that two CTAs fit on an SM.
-  h->stages = P.dtype == JACOBI_F64 ? 3 : 4;
+  // Ring depth of the plane-streaming path: four stages keep one plane in
+  // flight beyond the three a consumer reads (the autotuner may pick more).
+  h->stages = 4;
+  if (const char* em = getenv("JACOBI_FP64_EMU")) h->fp64_emu = atoi(em) != 0 ? 1 : 0;
   if (const char* st = getenv("JACOBI_STAGES")) {
     const int v = atoi(st);
     if (v >= 3 && v <= 8) h->stages = v;
@@ -747,6 +776,7 @@ int jacobi_info(const jacobi_t* h, jacobi_info_t* out) {
   out->halo_bytes_per_iter = h->plan.halo_elems * (int64_t)h->plan.elem;
   out->workspace_bytes = h->plan.bytes;
   out->stages = h->stages;
+  out->fp64_int_adds = (h->plan.dtype == JACOBI_F64 && h->fp64_emu) ? 3 : 0;
   int kinds = 0;
   for (int k = 0; k < kItemKinds; ++k) kinds += h->kind_off[k + 1] > h->kind_off[k] ? 1 : 0;
   out->item_kinds = kinds;
@@ -1051,6 +1081,45 @@ int jacobi_copy_out(jacobi_t* h, int64_t grid, void* dst, int32_t dst_on_device,
   if (e == cudaSuccess && tmp) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) rc = set_error(JACOBI_ECUDA, "copy_out failed: %s", cudaGetErrorString(e));
   return rc;
+}
+
+int jacobi_selftest_dadd(const double* a, const double* b, int64_t n, double* out, void* stream) {
+  if ((!a || !b || !out) && n > 0) return set_error(JACOBI_EINVAL, "null pointer");
+  if (n < 0) return set_error(JACOBI_EINVAL, "negative count");
+  JGB_CUDA(launch_selftest_dadd(a, b, n, out, S(stream)));
+  return JACOBI_OK;
+}
+
+int jacobi_pipe_rates(double* fp64_adds_per_s, double* int_adds_per_s, void* stream) {
+  const cudaStream_t s = S(stream);
+  int dev = 0, sms = 0;
+  JGB_CUDA(cudaGetDevice(&dev));
+  JGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int threads = 256, blocks = sms * 8, iters = 1024;
+  double* out = nullptr;
+  JGB_CUDA(cudaMalloc(&out, (size_t)blocks * threads * sizeof(double)));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double rate[2] = {0.0, 0.0};
+  cudaError_t e = cudaSuccess;
+  for (int emu = 0; emu < 2 && e == cudaSuccess; ++emu) {
+    e = launch_pipe_rate(emu != 0, blocks, threads, iters, out, s);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = launch_pipe_rate(emu != 0, blocks, threads, iters, out, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess) rate[emu] = (double)blocks * threads * iters * 8 / (ms * 1e-3);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (e != cudaSuccess) return set_error(JACOBI_ECUDA, "pipe-rate probe: %s", cudaGetErrorString(e));
+  if (fp64_adds_per_s) *fp64_adds_per_s = rate[0];
+  if (int_adds_per_s) *int_adds_per_s = rate[1];
+  return JACOBI_OK;
 }
 
 int jacobi_sync(jacobi_t* h, void* stream) {

@@ -41,14 +41,16 @@ struct BlockDev {
 
 // One CTA's share of a step over the z-range [z0, z1) of block `block`:
 //   x0 >= 0: the TX x TY tile of columns at (x0, y0);
-//   x0 <  0: whole x-y planes, streamed through shared memory, each thread
-//            computing y0 rows (1, 2, 4 or 8) of one 16-byte vector column.
+//   x0 <  0: rows [ya, yb) of the x-y planes, streamed through shared
+//            memory, each thread computing y0 rows (1, 2 or 4) of one
+//            16-byte vector column.
 // `slot` indexes the reduction partials.
 struct WorkItem {
   int32_t block;
   int32_t slot;
   int16_t x0, y0;
   int16_t z0, z1;
+  int16_t ya, yb;
 };
 
 // Per-grid state written by the host.
@@ -66,6 +68,8 @@ struct GridNorm {
   double r_norm2;       // |b - A u|^2 of the last residual evaluation
   double r_norm;        // sqrt(r_norm2)
   double rel;           // r_norm / |b| (r_norm when |b| == 0)
+  uint32_t emu_bad;     // FP64 state has a value outside dadd_nn's domain
+  uint32_t pad_;
 };
 
 // Tile shape of the table-driven kernels: 32 x 8 threads, each thread walks z.
@@ -78,6 +82,48 @@ __device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a,
 __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+
+// ---- FP64 addition on the integer pipe -----------------------------------------
+// On this GPU the FP64 pipe retires about 0.5 T adds/s, about the rate at
+// which the integer ALU pipe runs the routine below, and the two pipes run in
+// parallel; a stencil that spreads its FP64 adds over both raises its add
+// throughput.  dadd_nn returns exactly the IEEE-754 binary64 sum rounded to
+// nearest-even (bit-identical to __dadd_rn) for operands whose sign bit is
+// clear and whose exponent field is below 2040 (so no sum can overflow);
+// subnormals and zeros included.  Method: order the operands by their high
+// words (equal high words imply equal exponents, where the order does not
+// matter), take the 53-bit significands (hidden bit for normal numbers,
+// effective exponent max(e, 1)), place the larger at bit 62 of a 64-bit word
+// (10 guard bits), shift the smaller right by the exponent difference d
+// (clamped to 63), add, and renormalise by at most one bit.  Rounding to
+// nearest-even adds 0x1FF + (lsb | sticky) before dropping the 10 guard
+// bits, where sticky says that the alignment or renormalisation shift dropped
+// a nonzero bit: below half (guard bits < 0x200) never carries, above half
+// always carries, and exactly 0x200 carries iff the value is above the tie
+// (sticky) or the tie goes to the even neighbour (lsb).  The exponent is
+// added into the high word, so a rounding carry moves it correctly.
+__device__ __forceinline__ double dadd_nn(double a, double b) {
+  const uint64_t A = (uint64_t)__double_as_longlong(a), B = (uint64_t)__double_as_longlong(b);
+  const uint32_t ah = (uint32_t)(A >> 32), bh = (uint32_t)(B >> 32);
+  const bool sw = bh > ah;
+  const uint64_t X = sw ? B : A, Y = sw ? A : B;
+  const uint32_t ex = max((uint32_t)(X >> 52), 1u), ey = max((uint32_t)(Y >> 52), 1u);
+  const uint64_t mx = X - ((uint64_t)(ex - 1u) << 52);
+  const uint64_t my = Y - ((uint64_t)(ey - 1u) << 52);
+  const uint32_t d = min(ex - ey, 63u);
+  const uint64_t ys = my << 10;
+  const uint64_t ya = ys >> d;
+  uint64_t Z = (mx << 10) + ya;
+  const uint32_t s = (uint32_t)(Z >> 63);
+  const uint32_t sticky = (uint32_t)((ya << d) != ys) | ((uint32_t)Z & s);
+  Z >>= s;
+  const uint32_t lo = (uint32_t)Z;
+  Z += 0x1FFu + (((lo >> 10) | sticky) & 1u);
+  return __longlong_as_double((long long)((Z >> 10) + ((uint64_t)(ex + s - 1u) << 52)));
+}
+
+// High-word bound of the values dadd_nn accepts: sign clear, exponent < 2040.
+constexpr uint32_t kEmuHiLimit = 0x7F800000u;
 
 template <typename T> struct C6;
 template <> struct C6<double> { static constexpr double v = 1.0 / 6.0; };

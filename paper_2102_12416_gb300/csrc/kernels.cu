@@ -184,6 +184,57 @@ __global__ void __launch_bounds__(kThreads) k_bnorm(StepLaunch a) {
   if (threadIdx.x == 0) a.partials[w.slot] = s;
 }
 
+// Flag every FP64 grid whose current state (interior at its parity and all six
+// receive slots) holds a value outside the domain of the integer-pipe adder
+// dadd_nn; the step kernels then keep that grid on the FP64 pipe.  By the
+// discrete maximum principle Jacobi iterates stay within the range of the
+// boundary and initial data, so a state that passes keeps passing.
+__global__ void k_emu_check(const BlockDev* __restrict__ blocks, const GridDev* grids, GridNorm* norms, int64_t it) {
+  const BlockDev& B = blocks[blockIdx.x];
+  const int p = (int)((it - grids[B.grid].start_iter) & 1);
+  const uint32_t* U = (const uint32_t*)B.u[p];
+  bool bad = false;
+  const int64_t n = (int64_t)B.nx * B.ny;
+  for (int64_t k = 0; k < B.nz && !bad; ++k)
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) bad |= U[2 * (k * B.plane_pitch + e) + 1] >= kEmuHiLimit;
+  for (int f = 0; f < 6; ++f) {
+    const uint32_t* S = (const uint32_t*)B.recv[f][p];
+    const int64_t m = face_elems(B, f);
+    for (int64_t e = threadIdx.x; e < m; e += blockDim.x) bad |= S[2 * e + 1] >= kEmuHiLimit;
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&norms[B.grid].emu_bad, 1u);
+}
+
+__global__ void k_emu_reset(GridNorm* norms, const int32_t* grid_ids, int n) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) norms[grid_ids[q]].emu_bad = 0u;
+}
+
+// Self-test of the integer-pipe adder: out[i] = dadd_nn(a[i], b[i]).
+__global__ void k_selftest_dadd(const double* a, const double* b, int64_t n, double* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = i < n ? i : n - 1;  // every lane takes part in the adder's vote
+  const double r = dadd_nn(a[j], b[j]);
+  if (i < n) out[i] = r;
+}
+
+// Pipe-rate probe: chains of FP64 adds on the FP64 pipe (EMU = false) or
+// through dadd_nn on the integer pipe (EMU = true); 8 independent chains per
+// thread keep either pipe busy.  The result is stored so nothing is elided.
+template <bool EMU>
+__global__ void k_pipe_rate(double* out, int iters) {
+  double x[8];
+  for (int c = 0; c < 8; ++c) x[c] = 0.25 + 1e-3 * (double)(threadIdx.x + c);
+  const double inc = 1e-9 + 1e-13 * (double)blockIdx.x;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = EMU ? dadd_nn(x[c], inc) : __dadd_rn(x[c], inc);
+  }
+  double s = 0.0;
+  for (int c = 0; c < 8; ++c) s += x[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // One warp per grid: lane l sums slots item_begin + l, + l + 32, ... in order,
 // then a fixed butterfly combines the lanes.
 __global__ void k_reduce(const GridDev* grids, GridNorm* norms, const int32_t* grid_ids, const double* partials,
@@ -274,6 +325,25 @@ cudaError_t launch_copy_faces(const BlockDev* blocks, int32_t n_blocks, void* co
   const dim3 grid(n_blocks, 6);
   if (dtype == 0) k_copy_faces<double><<<grid, 256, 0, s>>>(blocks, staging, grids, it);
   else k_copy_faces<float><<<grid, 256, 0, s>>>(blocks, staging, grids, it);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emu_check(const BlockDev* blocks, int32_t n_blocks, const GridDev* grids, GridNorm* norms,
+                             const int32_t* grid_ids, int32_t n_grids, int64_t it, cudaStream_t s) {
+  if (n_grids > 0) k_emu_reset<<<(n_grids + 127) / 128, 128, 0, s>>>(norms, grid_ids, n_grids);
+  if (n_blocks > 0) k_emu_check<<<n_blocks, 256, 0, s>>>(blocks, grids, norms, it);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pipe_rate(bool emu, int blocks, int threads, int iters, double* out, cudaStream_t s) {
+  if (emu) k_pipe_rate<true><<<blocks, threads, 0, s>>>(out, iters);
+  else k_pipe_rate<false><<<blocks, threads, 0, s>>>(out, iters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_selftest_dadd(const double* a, const double* b, int64_t n, double* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_selftest_dadd<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, b, n, out);
   return cudaGetLastError();
 }
 

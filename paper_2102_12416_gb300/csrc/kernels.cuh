@@ -26,11 +26,11 @@ struct BlockGeom {
 // 227 KB per CTA, minus room for the kernels' static shared memory).
 constexpr int kMaxStepSmem = 227 * 1024 - 1024;  // 1 KB left for static shared memory
 
-// Item kinds of a step launch: 0 = tiles, 1..4 = plane streaming with 1, 2,
-// 4, 8 rows per thread.  Each kind runs its own kernel variant.
-constexpr int kItemKinds = 5;
+// Item kinds of a step launch: 0 = tiles, 1..3 = plane streaming with 1, 2,
+// 4 rows per thread.  Each kind runs its own kernel variant.
+constexpr int kItemKinds = 4;
 __host__ __device__ inline int item_kind(const WorkItem& w) {
-  return w.x0 >= 0 ? 0 : (w.y0 == 1 ? 1 : w.y0 == 2 ? 2 : w.y0 == 4 ? 3 : 4);
+  return w.x0 >= 0 ? 0 : (w.y0 == 1 ? 1 : w.y0 == 2 ? 2 : 3);
 }
 
 struct StepLaunch {
@@ -46,6 +46,9 @@ struct StepLaunch {
   int32_t smem;           // dynamic shared memory bytes (128 + stages * max stage)
   uint32_t* err;          // device error word (bounded waits)
   uint64_t wait_ns;
+  const GridNorm* norms;  // per-grid emu_bad flags (FP64 only; may be null)
+  int32_t emu;            // 1: FP64 pair sums may run on the integer pipe
+  int32_t pad_;
 };
 
 // Step kernels.  mode flags:
@@ -58,6 +61,13 @@ cudaError_t launch_pack_faces(const BlockDev* blocks, int32_t n_blocks, void* co
                               const GridDev* grids, int64_t it, int32_t dtype, cudaStream_t s);
 cudaError_t launch_copy_faces(const BlockDev* blocks, int32_t n_blocks, void* const* staging,
                               const GridDev* grids, int64_t it, int32_t dtype, cudaStream_t s);
+
+// Domain check of the integer-pipe FP64 adder (sets GridNorm::emu_bad) and
+// its self-test.
+cudaError_t launch_emu_check(const BlockDev* blocks, int32_t n_blocks, const GridDev* grids, GridNorm* norms,
+                             const int32_t* grid_ids, int32_t n_grids, int64_t it, cudaStream_t s);
+cudaError_t launch_selftest_dadd(const double* a, const double* b, int64_t n, double* out, cudaStream_t s);
+cudaError_t launch_pipe_rate(bool emu, int blocks, int threads, int iters, double* out, cudaStream_t s);
 
 // |b|^2 partials (interior = 0, only Dirichlet ghosts).
 cudaError_t launch_bnorm(const StepLaunch& a, cudaStream_t s);
@@ -98,6 +108,9 @@ struct PersistLaunch {
   int32_t dtype;
   int32_t stages;
   int32_t smem;
+  const GridNorm* norms;       // per-grid emu_bad flags (FP64 only)
+  int32_t emu;
+  int32_t pad_;
 };
 cudaError_t launch_persistent(const PersistLaunch& a, int grid_ctas, cudaStream_t s);
 int persistent_max_ctas(int dtype, int smem);  // co-resident CTA limit (0 on error)

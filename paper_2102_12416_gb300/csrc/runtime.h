@@ -128,6 +128,7 @@ struct jacobi_s {
 
   uint64_t wait_ns = 1000000000ull;
   int32_t stages = 4;             // ring stages of the plane-streaming path
+  int32_t fp64_emu = 1;           // FP64 pair sums on the integer pipe when safe
   int64_t drop_block = -1;        // fault injection (persistent path)
   void* stage = nullptr;          // device staging for host transfers
   size_t stage_bytes = 0;

@@ -229,6 +229,9 @@ int admit(serve_s* s, int si, const Req& q) {
   a.it = s->it;
   a.partials = s->d_partials;
   a.dtype = s->cfg.dtype;
+  if (s->cfg.dtype == JACOBI_F64)
+    ENG_CUDA(launch_emu_check(s->d_blocks + sl.block_base, (int32_t)nb, s->d_grids, s->d_norms, s->d_ids + si, 1,
+                              s->it, st));
   ENG_CUDA(launch_bnorm(a, st));
   ENG_CUDA(launch_reduce(s->d_grids, s->d_norms, s->d_ids + si, 1, s->d_partials, 1, st));
   ENG_CUDA(cudaStreamSynchronize(st));  // host staging vectors above are pageable
@@ -286,6 +289,8 @@ int run_round(serve_s* s) {
   a.smem = 128 + s->stages * (int32_t)s->max_stage;
   a.err = s->d_err;
   a.wait_ns = 1000000000ull;
+  a.norms = s->d_norms;
+  a.emu = 1;
   const int n = (int)s->running.size();
   for (int c = 0; c < s->cfg.round_checks; ++c) {
     a.it = s->it;
@@ -417,7 +422,7 @@ int serve_create(const serve_config* cfg, serve_t** out) {
   if (!s) return set_error(JACOBI_ENOMEM, "host allocation failed");
   s->cfg = *cfg;
   s->slots.resize(cfg->max_slots);
-  s->stages = cfg->dtype == JACOBI_F64 ? 3 : 4;
+  s->stages = 4;
   const int64_t ns = cfg->max_slots;
   size_t off = 0;
   auto take = [&](size_t b) { size_t o = off; off = align_up(off + b, 256); return o; };

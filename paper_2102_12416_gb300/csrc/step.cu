@@ -172,25 +172,85 @@ struct Ring {
   unsigned char* stages;
   uint64_t* bars;
   int S;
-  uint32_t pbits;  // parity of each stage's next fill (bit st)
+  uint32_t pbits;  // parity of each stage's next fill (bit st), barrier-driven form only
 };
 
-// Compute plane q of the item (k = z0 - 1 + q) from the stages holding planes
-// q - 1, q, q + 1.  Thread layout: tx = vector column, ty = group of RY rows.
-template <typename T, int RY, int MODE>
-__device__ __forceinline__ double stream_plane(const BlockDev& B, int p, int k, const unsigned char* sm,
-                                               const unsigned char* sc, const unsigned char* sp, int tx, int ty) {
+// Sum of the six neighbours in the stencil's order.  With EMU (FP64 states
+// inside the integer adder's domain) the three pair sums run on the integer
+// pipe and the two outer additions on the FP64 pipe: both pipes share the
+// work and the result is bit-identical.
+template <typename T, bool EMU>
+__device__ __forceinline__ T nsum(T xm, T xp, T ym, T yp, T zm, T zp) {
+  if (EMU) {
+    const double sx = dadd_nn((double)xm, (double)xp), sy = dadd_nn((double)ym, (double)yp),
+                 sz = dadd_nn((double)zm, (double)zp);
+    return (T)__dadd_rn(__dadd_rn(sx, sy), sz);
+  }
+  return radd(radd(radd(xm, xp), radd(ym, yp)), radd(zm, zp));
+}
+
+// Shared-memory stage of one plane of a row window [ya, yb) of block B: rows
+// ra..rb-1 of the plane (the window plus one neighbour row on each side that
+// exists), then the x ghosts of the window's rows (xm, xp), then the y ghost
+// rows (ym, yp; filled only at the block's edges, where they are needed).
+struct StageLayout {
+  int ra, rb;
+  uint32_t rows_bytes, xg, yg, bytes;
+  uint32_t o_xm, o_xp, o_ym, o_yp;
+};
+template <typename T>
+__device__ __forceinline__ StageLayout stage_layout(const BlockDev& B, int ya, int yb) {
+  StageLayout L;
+  L.ra = ya > 0 ? ya - 1 : 0;
+  L.rb = yb < B.ny ? yb + 1 : B.ny;
+  L.rows_bytes = (uint32_t)((L.rb - L.ra) * B.nx * sizeof(T));
+  L.xg = (uint32_t)((yb - ya) * sizeof(T));
+  L.yg = (uint32_t)(B.nx * sizeof(T));
+  L.o_xm = L.rows_bytes;
+  L.o_xp = L.o_xm + L.xg;
+  L.o_ym = L.o_xp + L.xg;
+  L.o_yp = L.o_ym + L.yg;
+  L.bytes = (L.o_yp + L.yg + 127u) & ~127u;
+  return L;
+}
+
+// Issue the bulk copies of plane q (k = z0 - 1 + q) of window [ya, yb) into
+// `dst`, completing on `bar`.
+template <typename T>
+__device__ __forceinline__ void issue_plane(const BlockDev& B, int p, int z0, int nplanes, int q, int ya, int yb,
+                                            const StageLayout& L, unsigned char* dst, uint64_t* bar) {
+  const int nx = B.nx, ny = B.ny, nz = B.nz;
+  const int kk = z0 - 1 + q;
+  const T* src = kk < 0 ? (const T*)B.recv[ZM][p]
+                        : (kk >= nz ? (const T*)B.recv[ZP][p] : (const T*)B.u[p] + (int64_t)kk * B.plane_pitch);
+  const bool ghosts = q >= 1 && q <= nplanes - 2;
+  const bool gym = ghosts && ya == 0, gyp = ghosts && yb == ny;
+  mbar_expect_tx(bar, L.rows_bytes + (ghosts ? 2 * L.xg : 0) + (gym ? L.yg : 0) + (gyp ? L.yg : 0));
+  bulk_g2s(dst, src + (int64_t)L.ra * nx, L.rows_bytes, bar);
+  if (ghosts) {
+    bulk_g2s(dst + L.o_xm, (const T*)B.recv[XM][p] + (int64_t)kk * ny + ya, L.xg, bar);
+    bulk_g2s(dst + L.o_xp, (const T*)B.recv[XP][p] + (int64_t)kk * ny + ya, L.xg, bar);
+  }
+  if (gym) bulk_g2s(dst + L.o_ym, (const T*)B.recv[YM][p] + (int64_t)kk * nx, L.yg, bar);
+  if (gyp) bulk_g2s(dst + L.o_yp, (const T*)B.recv[YP][p] + (int64_t)kk * nx, L.yg, bar);
+}
+
+// Compute plane k of rows [j0, j0 + RY) (inside the window [ya, yb)) from the
+// stages holding planes k - 1, k, k + 1.  tx = vector column.
+template <typename T, int RY, int MODE, bool EMU>
+__device__ __forceinline__ double stream_plane(const BlockDev& B, int p, int k, int ya, const StageLayout& L,
+                                               const unsigned char* sm, const unsigned char* sc,
+                                               const unsigned char* sp, int tx, int j0) {
   constexpr int VEC = V16<T>::N;
   const int nx = B.nx, ny = B.ny, nz = B.nz;
-  const int i0 = tx * VEC, j0 = ty * RY;
-  const size_t plane_bytes = (size_t)nx * ny * sizeof(T);
-  const T* Pm = (const T*)sm;
-  const T* Pc = (const T*)sc;
-  const T* Pp = (const T*)sp;
-  const T* Gxm = (const T*)(sc + plane_bytes);
-  const T* Gxp = Gxm + ny;
-  const T* Gym = Gxp + ny;
-  const T* Gyp = Gym + nx;
+  const int i0 = tx * VEC;
+  const T* Pm = (const T*)sm - L.ra * nx;  // row j of a plane at P + j * nx
+  const T* Pc = (const T*)sc - L.ra * nx;
+  const T* Pp = (const T*)sp - L.ra * nx;
+  const T* Gxm = (const T*)(sc + L.o_xm) - ya;  // x ghost of row j at G[j]
+  const T* Gxp = (const T*)(sc + L.o_xp) - ya;
+  const T* Gym = (const T*)(sc + L.o_ym);
+  const T* Gyp = (const T*)(sc + L.o_yp);
   T* __restrict__ V = (T*)B.u[p ^ 1] + (int64_t)k * B.plane_pitch;
 
   T c[RY][VEC];
@@ -215,7 +275,7 @@ __device__ __forceinline__ double stream_plane(const BlockDev& B, int p, int k, 
     for (int q = 0; q < VEC; ++q) {
       const T xm = q == 0 ? left : c[r][q > 0 ? q - 1 : 0];
       const T xp = q == VEC - 1 ? right : c[r][q < VEC - 1 ? q + 1 : 0];
-      const T s = radd(radd(radd(xm, xp), radd(ym[q], yp[q])), radd(zm[q], zp[q]));
+      const T s = nsum<T, EMU>(xm, xp, ym[q], yp[q], zm[q], zp[q]);
       v[q] = rmul(s, C6<T>::v);
       if (MODE & kResid) acc += resid2<T>(xm, xp, ym[q], yp[q], zm[q], zp[q], s, c[r][q]);
     }
@@ -252,63 +312,36 @@ __device__ __forceinline__ double stream_plane(const BlockDev& B, int p, int k, 
   return acc;
 }
 
-// Bytes of one ring stage for block B: the plane and its four x/y ghost
-// vectors, rounded up to 128 bytes.
-template <typename T>
-__device__ __forceinline__ uint32_t stage_bytes_of(const BlockDev& B) {
-  const uint32_t plane = (uint32_t)(B.nx * B.ny * sizeof(T));
-  const uint32_t g = (uint32_t)(2 * (B.nx + B.ny) * sizeof(T));
-  return (plane + g + 127u) & ~127u;
-}
-
-// Stream planes [z0, z1) of block B through the ring.  All threads of the CTA
-// call it.  Returns this thread's r^2 sum; sets ok = false (CTA-uniform) after
-// a bounded wait expired (the error word is set and issued copies drained).
+// Barrier-driven form of the streaming sweep, used inside the persistent
+// kernel (all threads call it; one thread issues the copies).  Returns this
+// thread's r^2 sum; sets ok = false (CTA-uniform) after a bounded wait
+// expired (the error word is set and issued copies drained).
 template <typename T, int RY, int MODE>
-__device__ double stream_item(const BlockDev& B, int p, int z0, int z1, Ring& ring, uint32_t* err,
-                              uint64_t wait_ns, bool& ok) {
+__device__ double stream_item(const BlockDev& B, int p, const WorkItem& w, Ring& ring, uint32_t* err,
+                              uint64_t wait_ns, bool emu, bool& ok) {
   constexpr int VEC = V16<T>::N;
-  const int nx = B.nx, ny = B.ny, nz = B.nz;
   const int tid = threadIdx.x;
-  const int txv = nx / VEC;
-  const int tx = tid % txv, ty = tid / txv;
-  const bool active = ty * RY < ny;
+  const int txv = B.nx / VEC;
+  const int tx = tid % txv, j0 = w.ya + (tid / txv) * RY;
+  const bool active = j0 < w.yb;
   const int S = ring.S;
-  const uint32_t sbytes = stage_bytes_of<T>(B);
-  const uint32_t plane_bytes = (uint32_t)(nx * ny * sizeof(T));
-  const uint32_t xg = (uint32_t)(ny * sizeof(T)), yg = (uint32_t)(nx * sizeof(T));
-  const T* U = (const T*)B.u[p];
-  const int nplanes = z1 - z0 + 2;  // planes z0-1 .. z1
-
+  const StageLayout L = stage_layout<T>(B, w.ya, w.yb);
+  const int nplanes = w.z1 - w.z0 + 2;
   auto issue = [&](int q) {
     const int st = q % S;
-    unsigned char* dst = ring.stages + (size_t)st * sbytes;
-    const int kk = z0 - 1 + q;
-    const T* src = kk < 0 ? (const T*)B.recv[ZM][p] : (kk >= nz ? (const T*)B.recv[ZP][p] : U + (int64_t)kk * B.plane_pitch);
-    const bool ghosts = q >= 1 && q <= nplanes - 2;
-    uint64_t* bar = ring.bars + st;
-    mbar_expect_tx(bar, plane_bytes + (ghosts ? 2 * (xg + yg) : 0));
-    bulk_g2s(dst, src, plane_bytes, bar);
-    if (ghosts) {
-      bulk_g2s(dst + plane_bytes, (const T*)B.recv[XM][p] + (int64_t)kk * ny, xg, bar);
-      bulk_g2s(dst + plane_bytes + xg, (const T*)B.recv[XP][p] + (int64_t)kk * ny, xg, bar);
-      bulk_g2s(dst + plane_bytes + 2 * xg, (const T*)B.recv[YM][p] + (int64_t)kk * nx, yg, bar);
-      bulk_g2s(dst + plane_bytes + 2 * xg + yg, (const T*)B.recv[YP][p] + (int64_t)kk * nx, yg, bar);
-    }
+    issue_plane<T>(B, p, w.z0, nplanes, q, w.ya, w.yb, L, ring.stages + (size_t)st * L.bytes, ring.bars + st);
   };
   auto wait = [&](int q) {
     const int st = q % S;
     const uint32_t parity = ((ring.pbits >> st) ^ (uint32_t)(q / S)) & 1u;
     return mbar_wait(ring.bars + st, parity, err, wait_ns);
   };
-
-  int issued = 0;
   if (tid == 0) {
     fence_proxy_async();
     const int n0 = min(S - 1, nplanes);
     for (int q = 0; q < n0; ++q) issue(q);
   }
-  issued = min(S - 1, nplanes);
+  int issued = min(S - 1, nplanes);
   double acc = 0.0;
   bool good = true;
   for (int q = 1; q <= nplanes - 2; ++q) {
@@ -325,10 +358,13 @@ __device__ double stream_item(const BlockDev& B, int p, int z0, int z1, Ring& ri
     if (q == 1) good = wait(0) && wait(1);
     good = good && wait(q + 1);
     if (good && active) {
-      const unsigned char* sm = ring.stages + (size_t)((q - 1) % S) * sbytes;
-      const unsigned char* sc = ring.stages + (size_t)(q % S) * sbytes;
-      const unsigned char* sp = ring.stages + (size_t)((q + 1) % S) * sbytes;
-      acc += stream_plane<T, RY, MODE>(B, p, z0 - 1 + q, sm, sc, sp, tx, ty);
+      const unsigned char* sm = ring.stages + (size_t)((q - 1) % S) * L.bytes;
+      const unsigned char* sc = ring.stages + (size_t)(q % S) * L.bytes;
+      const unsigned char* sp = ring.stages + (size_t)((q + 1) % S) * L.bytes;
+      if (sizeof(T) == 8 && emu)
+        acc += stream_plane<T, RY, MODE, true>(B, p, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
+      else
+        acc += stream_plane<T, RY, MODE, false>(B, p, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
     }
   }
   ok = __syncthreads_and(good) != 0;
@@ -350,14 +386,13 @@ __device__ double stream_item(const BlockDev& B, int p, int z0, int z1, Ring& ri
 
 template <typename T, int MODE>
 __device__ double run_item(const BlockDev& B, int p, const WorkItem& w, Ring& ring, uint32_t* err,
-                           uint64_t wait_ns, bool& ok) {
+                           uint64_t wait_ns, bool emu, bool& ok) {
   ok = true;
   if (w.x0 >= 0) return tile_sweep<T, MODE>(B, p, w.x0, w.y0, w.z0, w.z1, threadIdx.x % TX, threadIdx.x / TX);
   switch (w.y0) {
-    case 1: return stream_item<T, 1, MODE>(B, p, w.z0, w.z1, ring, err, wait_ns, ok);
-    case 2: return stream_item<T, 2, MODE>(B, p, w.z0, w.z1, ring, err, wait_ns, ok);
-    case 4: return stream_item<T, 4, MODE>(B, p, w.z0, w.z1, ring, err, wait_ns, ok);
-    default: return stream_item<T, 8, MODE>(B, p, w.z0, w.z1, ring, err, wait_ns, ok);
+    case 1: return stream_item<T, 1, MODE>(B, p, w, ring, err, wait_ns, emu, ok);
+    case 2: return stream_item<T, 2, MODE>(B, p, w, ring, err, wait_ns, emu, ok);
+    default: return stream_item<T, 4, MODE>(B, p, w, ring, err, wait_ns, emu, ok);
   }
 }
 
@@ -407,7 +442,7 @@ constexpr int kStreamThreads = kThreads + 32;
 
 template <typename T> struct StreamOcc;
 template <> struct StreamOcc<float> { static constexpr int min_blocks = 3; };
-template <> struct StreamOcc<double> { static constexpr int min_blocks = 2; };
+template <> struct StreamOcc<double> { static constexpr int min_blocks = 3; };
 
 template <typename T, int RY, int MODE>
 __global__ void __launch_bounds__(kStreamThreads, StreamOcc<T>::min_blocks) k_stream(StepLaunch a) {
@@ -423,10 +458,8 @@ __global__ void __launch_bounds__(kStreamThreads, StreamOcc<T>::min_blocks) k_st
   const int p = (int)((a.it - G.start_iter) & 1);
   const int S = a.stages;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nx = B.nx, ny = B.ny, nz = B.nz;
-  const int z0 = w.z0, z1 = w.z1;
-  const int nplanes = z1 - z0 + 2;  // planes z0-1 .. z1
-  const uint32_t sbytes = stage_bytes_of<T>(B);
+  const int nplanes = w.z1 - w.z0 + 2;  // planes z0-1 .. z1
+  const StageLayout L = stage_layout<T>(B, w.ya, w.yb);
   if (tid == 0) {
     for (int st = 0; st < S; ++st) {
       mbar_init(full + st, 1);
@@ -439,28 +472,12 @@ __global__ void __launch_bounds__(kStreamThreads, StreamOcc<T>::min_blocks) k_st
   if (warp == kConsumerWarps) {
     // ---- producer ----
     if (lane == 0) {
-      const uint32_t plane_bytes = (uint32_t)(nx * ny * sizeof(T));
-      const uint32_t xg = (uint32_t)(ny * sizeof(T)), yg = (uint32_t)(nx * sizeof(T));
-      const T* U = (const T*)B.u[p];
       int q = 0;
       for (; q < nplanes; ++q) {
         const int st = q % S, fill = q / S;
         if (fill > 0 && !mbar_wait(empty + st, (uint32_t)(fill - 1) & 1u, a.err, a.wait_ns)) break;
         fence_proxy_async();
-        unsigned char* dst = stages + (size_t)st * sbytes;
-        const int kk = z0 - 1 + q;
-        const T* src = kk < 0 ? (const T*)B.recv[ZM][p]
-                              : (kk >= nz ? (const T*)B.recv[ZP][p] : U + (int64_t)kk * B.plane_pitch);
-        const bool ghosts = q >= 1 && q <= nplanes - 2;
-        uint64_t* bar = full + st;
-        mbar_expect_tx(bar, plane_bytes + (ghosts ? 2 * (xg + yg) : 0));
-        bulk_g2s(dst, src, plane_bytes, bar);
-        if (ghosts) {
-          bulk_g2s(dst + plane_bytes, (const T*)B.recv[XM][p] + (int64_t)kk * ny, xg, bar);
-          bulk_g2s(dst + plane_bytes + xg, (const T*)B.recv[XP][p] + (int64_t)kk * ny, xg, bar);
-          bulk_g2s(dst + plane_bytes + 2 * xg, (const T*)B.recv[YM][p] + (int64_t)kk * nx, yg, bar);
-          bulk_g2s(dst + plane_bytes + 2 * xg + yg, (const T*)B.recv[YP][p] + (int64_t)kk * nx, yg, bar);
-        }
+        issue_plane<T>(B, p, w.z0, nplanes, q, w.ya, w.yb, L, stages + (size_t)st * L.bytes, full + st);
       }
       if (q < nplanes) {
         // A wait expired: let the copies already issued land before leaving.
@@ -473,22 +490,27 @@ __global__ void __launch_bounds__(kStreamThreads, StreamOcc<T>::min_blocks) k_st
     }
   } else {
     // ---- consumers ----
-    const int txv = nx / VEC;
-    const int tx = tid % txv, ty = tid / txv;
-    const bool active = ty * RY < ny;
+    const bool emu = sizeof(T) == 8 && a.emu && a.norms && a.norms[B.grid].emu_bad == 0u;
+    const int txv = B.nx / VEC;
+    const int tx = tid % txv, j0 = w.ya + (tid / txv) * RY;
+    const bool active = j0 < w.yb;
     bool good = true;
     for (int q = 1; q <= nplanes - 2 && good; ++q) {
       if (q == 1) {
-        good = mbar_wait(full + 0, 0u, a.err, a.wait_ns) && mbar_wait(full + 1 % S, (uint32_t)(1 / S) & 1u, a.err, a.wait_ns);
+        good = mbar_wait(full + 0, 0u, a.err, a.wait_ns) &&
+               mbar_wait(full + 1 % S, (uint32_t)(1 / S) & 1u, a.err, a.wait_ns);
       }
       good = good && mbar_wait(full + (q + 1) % S, (uint32_t)((q + 1) / S) & 1u, a.err, a.wait_ns);
       good = __all_sync(0xffffffffu, good);
       if (!good) break;
       if (active) {
-        const unsigned char* sm = stages + (size_t)((q - 1) % S) * sbytes;
-        const unsigned char* sc = stages + (size_t)(q % S) * sbytes;
-        const unsigned char* sp = stages + (size_t)((q + 1) % S) * sbytes;
-        acc += stream_plane<T, RY, MODE>(B, p, z0 - 1 + q, sm, sc, sp, tx, ty);
+        const unsigned char* sm = stages + (size_t)((q - 1) % S) * L.bytes;
+        const unsigned char* sc = stages + (size_t)(q % S) * L.bytes;
+        const unsigned char* sp = stages + (size_t)((q + 1) % S) * L.bytes;
+        if (sizeof(T) == 8 && emu)
+          acc += stream_plane<T, RY, MODE, true>(B, p, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
+        else
+          acc += stream_plane<T, RY, MODE, false>(B, p, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(empty + (q - 1) % S);
@@ -539,15 +561,16 @@ __global__ void __launch_bounds__(kThreads) k_persist(PersistLaunch a) {
       }
       const int p = (int)((it - a.grids[B.grid].start_iter) & 1);
       const bool resid = a.resid_first && t == 0;
+      const bool emu = sizeof(T) == 8 && a.emu && a.norms && a.norms[B.grid].emu_bad == 0u;
       for (int q = a.block_items[bi]; q < a.block_items[bi + 1]; ++q) {
         const WorkItem w = a.items[q];
         bool ok;
         if (resid) {
-          const double acc = run_item<T, kWrite | kPack | kResid>(B, p, w, ring, a.err, a.wait_ns, ok);
+          const double acc = run_item<T, kWrite | kPack | kResid>(B, p, w, ring, a.err, a.wait_ns, emu, ok);
           const double s = block_sum<kThreads>(acc, red);
           if (tid == 0) a.partials[w.slot] = s;
         } else {
-          run_item<T, kWrite | kPack>(B, p, w, ring, a.err, a.wait_ns, ok);
+          run_item<T, kWrite | kPack>(B, p, w, ring, a.err, a.wait_ns, emu, ok);
         }
         if (!ok) return;  // CTA-uniform
       }
@@ -590,8 +613,7 @@ cudaError_t launch_kinds(const StepLaunch& a, cudaStream_t s) {
       case 0: k_tiles<T, MODE><<<b.n_items, kThreads, 0, s>>>(b); e = cudaGetLastError(); break;
       case 1: e = launch_stream<T, 1, MODE>(b, s); break;
       case 2: e = launch_stream<T, 2, MODE>(b, s); break;
-      case 3: e = launch_stream<T, 4, MODE>(b, s); break;
-      default: e = launch_stream<T, 8, MODE>(b, s); break;
+      default: e = launch_stream<T, 4, MODE>(b, s); break;
     }
     if (e != cudaSuccess) return e;
   }

@@ -1,0 +1,88 @@
+"""The FP64 stencil's integer-pipe adder (dadd_nn) must equal IEEE-754
+round-to-nearest-even addition bit for bit on its domain (non-negative,
+exponent field < 2040); numpy's float64 addition is the reference.  And the
+step kernels give identical iterates whether the pair sums run on the integer
+pipe or on the FP64 pipe (JACOBI_FP64_EMU=0)."""
+import numpy as np
+import pytest
+
+import jacobi_inputs as J
+import paper_2102_12416_gb300 as jg
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2102_12416_gb300 import _build
+    _build.build()
+    jg.load()
+
+
+def _pairs(n, seed):
+    rng = np.random.default_rng(seed)
+    mant = rng.integers(0, 1 << 52, size=n, dtype=np.uint64)
+    kind = rng.integers(0, 6, size=n)
+    exp = np.where(kind == 0, 1023 - rng.integers(0, 40, size=n),          # [2^-39, 2)
+          np.where(kind == 1, 1 + rng.integers(0, 2039, size=n),            # any normal < 2040
+          np.where(kind == 2, 0,                                            # subnormal
+                   1023 - rng.integers(0, 3, size=n)))).astype(np.uint64)   # near 1
+    short = kind >= 4                                                       # few mantissa bits
+    cut = rng.integers(0, 53, size=n).astype(np.uint64)
+    mant = np.where(short, mant & ~((np.uint64(1) << cut) - np.uint64(1)), mant)
+    a_bits = (exp << np.uint64(52)) | mant
+    gap = rng.integers(0, 71, size=n).astype(np.int64)
+    eb = np.maximum(exp.astype(np.int64) - gap, 0).astype(np.uint64)
+    mb = rng.integers(0, 1 << 52, size=n, dtype=np.uint64)
+    cutb = rng.integers(0, 53, size=n).astype(np.uint64)
+    mb = np.where(rng.random(n) < 0.3, mb & ~((np.uint64(1) << cutb) - np.uint64(1)), mb)
+    b_bits = (eb << np.uint64(52)) | mb
+    a, b = a_bits.view(np.float64).copy(), b_bits.view(np.float64).copy()
+    b[::11] = 0.0
+    b[::13] = a[::13]
+    # exact-tie patterns: b is half an ulp of a (times an odd factor of 2^k)
+    t = np.arange(0, n, 17)
+    b[t] = np.ldexp(np.ones(len(t)), np.frexp(a[t])[1] - 54) * (1 + 2 * (t % 3))
+    swap = rng.random(n) < 0.5
+    return np.where(swap, b, a), np.where(swap, a, b)
+
+
+def test_integer_pipe_adder_is_ieee_rne():
+    for seed in (1, 2, 3):
+        a, b = _pairs(1 << 22, seed)
+        assert (a >= 0).all() and (b >= 0).all()
+        want = (a + b).view(np.uint64)
+        da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+        out = torch.empty_like(da)
+        jg.jacobi_selftest_dadd(da.data_ptr(), db.data_ptr(), len(a), out.data_ptr())
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint64)
+        bad = np.nonzero(got != want)[0]
+        assert len(bad) == 0, [(a[i].hex(), b[i].hex()) for i in bad[:4]]
+
+
+def test_stencil_same_with_and_without_integer_adds(monkeypatch):
+    grid, split = (96, 80, 72), ("shape", (32, 16, 24))
+    init = dict(bc="uniform", bc_seed=5, interior="uniform", interior_seed=6)
+    outs = []
+    for emu in ("1", "0"):
+        monkeypatch.setenv("JACOBI_FP64_EMU", emu)
+        with jg.Jacobi3D(grid, split, "f64", init, path="graph") as s:
+            s.step(150)
+            rel, _ = s.residual()
+            outs.append((s.copy_out(), rel[0]))
+    assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+
+
+def test_negative_values_keep_the_fp64_pipe(oracle_mod):
+    """A boundary with negative values is outside the adder's domain: the grid
+    runs on the FP64 pipe and still matches the oracle."""
+    nx, ny, nz = 40, 36, 32
+    u = J.initial_grid(nx, ny, nz, "uniform", bc_seed=9, interior="uniform", interior_seed=10) - 0.5
+    with jg.Jacobi3D((nx, ny, nz), ("shape", (16, 16, 16)), "f64") as s:
+        s.set_state(u)
+        s.step(40)
+        got = s.copy_out()
+    assert np.array_equal(got, J.interior_of(oracle_mod.jacobi(u, 40)))

@@ -70,7 +70,7 @@ def measured_peaks():
 
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    for name in ("kernels.cu", "common.cuh", "kernels.cuh"):
+    for name in ("step.cu", "kernels.cu", "common.cuh", "kernels.cuh"):
         with open(os.path.join(ROOT, "paper_2102_12416_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

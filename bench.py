@@ -54,6 +54,8 @@ def parse_args():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--serve-requests", type=int, default=200,
                    help="requests of the serving workload to run (0 = skip; 10000 = the full workload)")
+    p.add_argument("--precision", action="store_true",
+                   help="also run the FP32-state precision study (768^3 and 96^3/192^3 proxies)")
     p.add_argument("--serve-baseline", type=int, default=100,
                    help="requests re-solved by the plain per-grid FP64 launch loop")
     return p.parse_args()
@@ -238,7 +240,7 @@ def channel_sweep(jg, torch, s, stream):
     try:
         for k in range(20):
             nbytes = 8 << k
-            ctas = max(1, min(64, nbytes // (128 << 10)))
+            ctas = max(1, min(128, nbytes // (16 << 10)))
             rounds = 2000 if nbytes <= (64 << 10) else 200
             jg.channel_pingpong(ch, nbytes, 50, ctas, stream)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -319,6 +321,124 @@ def serving_bench(jg, J, n_requests, n_baseline):
         out["fp64_launch_loop"] = {"requests": nb, "solves_per_s": nb / bt, "wall_s": bt, "statuses": base_status,
                                    "note": "one kernel launch per iteration, residual read on the host at each check"}
         out["served_solves_per_s_vs_launch_loop"] = out["solves_per_s"] / (nb / bt)
+    return out
+
+
+def channel_modes(jg, torch, s, stream):
+    """One-way latency of the three exchange forms the paper compares (Sec.
+    4.2.1), all between the same two blocks of one GPU: the device channel
+    driven from the host (send + receive kernels, completion by stream sync),
+    the GPU Messaging form (the device copy is posted only after a host-side
+    metadata message) and host staging (device->host, host hand-off,
+    host->device).  The device-resident ping-pong above is the channel with no
+    host in the loop at all."""
+    nmax = 4 << 20
+    ch = jg.channel_open(s.h, 2, 0, 1, nmax)
+    src = torch.zeros(nmax, dtype=torch.uint8, device="cuda")
+    dst = torch.zeros(nmax, dtype=torch.uint8, device="cuda")
+    out = []
+    try:
+        for k in range(0, 20, 2):
+            n = 8 << k
+            rounds = 200 if n <= (64 << 10) else 20
+            row = {"bytes": n}
+            for mode in ("channel", "messaging", "host_staged"):
+                for warm in (True, False):
+                    t0 = time.perf_counter()
+                    for _ in range(rounds if not warm else 5):
+                        for a, b in ((0, 1), (1, 0)):
+                            if mode == "channel":
+                                jg.channel_send(ch, a, src.data_ptr(), n, stream)
+                                jg.channel_recv(ch, b, dst.data_ptr(), n, stream)
+                                stream.synchronize()
+                            elif mode == "messaging":
+                                jg.channel_send_msg(ch, a, src.data_ptr(), n, stream)
+                                jg.channel_recv_msg(ch, b, dst.data_ptr(), n, stream)
+                            else:
+                                jg.channel_send_host(ch, a, src.data_ptr(), n, stream)
+                                jg.channel_recv_host(ch, b, dst.data_ptr(), n, stream)
+                    dt = time.perf_counter() - t0
+                row[mode + "_us"] = round(dt * 1e6 / (2 * rounds), 2)
+            jg.channel_sync(ch, stream)  # device-side errors of this size, once
+            out.append(row)
+    finally:
+        jg.channel_close(ch)
+    return out
+
+
+def channel_bw(jg, torch, s, stream):
+    """OSU-style window bandwidth (window 64) between two blocks' channel
+    endpoints, one-directional and bidirectional, 8 B .. 4 MB."""
+    ch = jg.channel_open(s.h, 3, 0, 1, 4 << 20)
+    out = []
+    try:
+        for k in range(0, 20, 2):
+            n = 8 << k
+            ctas = max(1, min(128, n // (16 << 10)))
+            iters = 20
+            row = {"bytes": n, "window": 64, "ctas_per_side": ctas}
+            for bidir in (False, True):
+                jg.channel_bandwidth(ch, n, 64, 2, ctas, bidir, stream)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                jg.channel_bandwidth(ch, n, 64, iters, ctas, bidir, stream)
+                e1.record(stream)
+                e1.synchronize()
+                jg.channel_sync(ch, stream)
+                sec = e0.elapsed_time(e1) * 1e-3
+                row["bidir_GBps" if bidir else "GBps"] = round((2 if bidir else 1) * 64 * iters * n / sec / 1e9, 3)
+            out.append(row)
+    finally:
+        jg.channel_close(ch)
+    return out
+
+
+def precision_study(jg, J, np):
+    """FP32 state with FP64 residual against the FP64 path (bit-exact with the
+    oracle by the parity tests).  (1) The 768^3 workload (12^3 blocks of 64^3)
+    after a fixed number of iterations: relative inf-norm difference.  (2)
+    Proxies 96^3 and 192^3 split 12x12x12 the same way, solved to 1e-6
+    relative residual: iterations, status, achieved residual and the error of
+    the FP32 solution against the FP64 solution at the same tolerance and
+    against the FP64 solution converged to 1e-12."""
+    w = J.WORKLOADS["jacobi3d-fp32-768c-12x12x12"]
+    init = dict(bc=w["bc"], bc_seed=w["bc_seed"], noise_amp=w["noise_amp"], interior=w["interior"])
+    out = {"tol": 1e-6, "check_every": 100}
+    its = 2000
+    res = {}
+    for dt in ("f32", "f64"):
+        with jg.Jacobi3D(w["grid"], w["split"], dt, init, path="graph") as s:
+            s.step(its)
+            rel, _ = s.residual()
+            res[dt] = (s.copy_out().astype(np.float64), rel[0])
+    ref = res["f64"][0]
+    out["full_768c"] = {"iterations": its, "rel_f32": res["f32"][1], "rel_f64": res["f64"][1],
+                        "err_f32_vs_f64": float(np.max(np.abs(res["f32"][0] - ref)) / np.max(np.abs(ref))),
+                        "iterations_to_tol_estimate": int(np.ceil(np.log(1e6) / (1 - np.cos(np.pi / 769))))}
+    del res, ref
+    for n in (96, 192):
+        grid, split = (n, n, n), ("count", (12, 12, 12))
+        row = {}
+        sols = {}
+        for dt, tol in (("f32", 1e-6), ("f64", 1e-6), ("f64_exact", 1e-12)):
+            d = "f64" if dt.startswith("f64") else "f32"
+            with jg.Jacobi3D(grid, split, d, init, path="graph") as s:
+                t0 = time.perf_counter()
+                it, rel, st = s.solve(tol, 2_000_000, 100, stall_checks=50)
+                sec = time.perf_counter() - t0
+                sols[dt] = s.copy_out().astype(np.float64)
+            row[dt] = {"iterations": it[0], "rel": rel[0], "status": ("converged", "max_iters", "stagnated")[st[0]],
+                       "seconds": round(sec, 3)}
+        ex = sols["f64_exact"]
+        scale = np.max(np.abs(ex))
+        with jg.Jacobi3D(grid, split, "f64", init, path="graph") as s:
+            s.step(row["f32"]["iterations"])
+            same_it = s.copy_out().astype(np.float64)
+        row["err_f32_vs_f64_same_iterations"] = float(np.max(np.abs(sols["f32"] - same_it)) / np.max(np.abs(same_it)))
+        row["err_f32_vs_f64_same_tol"] = float(np.max(np.abs(sols["f32"] - sols["f64"])) / np.max(np.abs(sols["f64"])))
+        row["err_f32_vs_converged"] = float(np.max(np.abs(sols["f32"] - ex)) / scale)
+        row["err_f64_vs_converged"] = float(np.max(np.abs(sols["f64"] - ex)) / scale)
+        out[f"proxy_{n}c"] = row
     return out
 
 
@@ -450,11 +570,18 @@ def run_ours(args):
            "d2h_bytes_per_step": sum(x.numel() * x.element_size() for x in h_out) + 16 * len(grids),
            "steps": e2e_steps}
 
-    sweep = None
+    sweep = modes = bw = None
     if not args.no_sweep and rank == 0:
         sweep = channel_sweep(jg, torch, s, stream)
+        modes = channel_modes(jg, torch, s, stream)
+        bw = channel_bw(jg, torch, s, stream)
     s.close()
     del h_in, h_out
+
+    precision = None
+    if rank == 0 and args.precision:
+        import numpy as np
+        precision = precision_study(jg, J, np)
 
     serving = None
     if rank == 0 and args.serve_requests > 0:
@@ -474,7 +601,8 @@ def run_ours(args):
                                parallelism=f"replicas{world}" if world > 1 else "single-gpu", autotune=tuned),
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "halo": halo, "final_rel_residual": rel[0] if rel else None,
-                "channel_pingpong": sweep, "serving": serving}
+                "channel_pingpong": sweep, "channel_modes": modes, "channel_bandwidth": bw,
+                "serving": serving, "precision": precision}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -367,6 +367,34 @@ int channel_sync(channel_t* ch, void* stream);
 int channel_pingpong(channel_t* ch, size_t bytes, int64_t round_trips, int32_t ctas_per_side,
                      void* stream);
 
+/* OSU-style bandwidth test (Sec. 4.2.2), run on the device: one cooperative
+ * launch in which endpoint a sends `window` messages of `bytes` back to back
+ * into b's slot and b acknowledges, `iterations` times (with bidirectional set
+ * both endpoints send a window per iteration).  Sources are each endpoint's
+ * parity-1 slot.  The caller times the launch: bandwidth = (1 or 2) * window *
+ * iterations * bytes / elapsed. */
+int channel_bandwidth(channel_t* ch, size_t bytes, int32_t window, int64_t iterations, int32_t ctas_per_side,
+                      int32_t bidirectional, void* stream);
+
+/* The two comparison forms of the paper, for benchmarks against the channel.
+ *
+ * Host staging (Fig. 9, the non-GPU-aware path): channel_send_host copies the
+ * payload device->host into a pinned staging buffer of the receiving endpoint
+ * and waits for it; channel_recv_host copies it host->device into dst and
+ * waits.  Both synchronise the stream; one host-staged message may be in
+ * flight per direction.
+ *
+ * GPU Messaging (Sec. 3.2.1): channel_send_msg only posts a host-side
+ * metadata message (source address, size, sequence number) to the peer's
+ * mailbox; channel_recv_msg takes the oldest one -- the receive can only be
+ * posted once the metadata has arrived -- issues the device copy src -> dst and
+ * waits for it.  JACOBI_EAGAIN when no metadata message is waiting,
+ * JACOBI_ESEQ on a size mismatch.  The source must stay valid until received. */
+int channel_send_host(channel_t* ch, int64_t from_block, const void* src, size_t bytes, void* stream);
+int channel_recv_host(channel_t* ch, int64_t at_block, void* dst, size_t bytes, void* stream);
+int channel_send_msg(channel_t* ch, int64_t from_block, const void* src, size_t bytes, void* stream);
+int channel_recv_msg(channel_t* ch, int64_t at_block, void* dst, size_t bytes, void* stream);
+
 int channel_close(channel_t* ch);
 
 /* ---- serving: continuous batching of solve requests --------------------------- */

@@ -135,6 +135,11 @@ _SIGS = {
     "channel_sync": (ctypes.c_int, [P, P]),
     "channel_pingpong": (ctypes.c_int, [P, c_size_t, c_int64, c_int32, P]),
     "channel_close": (ctypes.c_int, [P]),
+    "channel_bandwidth": (ctypes.c_int, [P, c_size_t, c_int32, c_int64, c_int32, c_int32, P]),
+    "channel_send_host": (ctypes.c_int, [P, c_int64, P, c_size_t, P]),
+    "channel_recv_host": (ctypes.c_int, [P, c_int64, P, c_size_t, P]),
+    "channel_send_msg": (ctypes.c_int, [P, c_int64, P, c_size_t, P]),
+    "channel_recv_msg": (ctypes.c_int, [P, c_int64, P, c_size_t, P]),
     "serve_create": (ctypes.c_int, [ctypes.POINTER(serve_config), ctypes.POINTER(P)]),
     "serve_submit": (ctypes.c_int, [P, ctypes.POINTER(serve_request), ctypes.POINTER(c_uint64)]),
     "serve_poll": (ctypes.c_int, [P, c_uint64, ctypes.POINTER(serve_result)]),
@@ -366,6 +371,27 @@ def channel_sync(ch, stream=None):
 
 def channel_pingpong(ch, nbytes, round_trips, ctas_per_side=1, stream=None):
     _call("channel_pingpong", ch, nbytes, round_trips, ctas_per_side, _stream(stream))
+
+
+def channel_bandwidth(ch, nbytes, window, iterations, ctas_per_side=1, bidirectional=False, stream=None):
+    _call("channel_bandwidth", ch, nbytes, window, iterations, ctas_per_side, 1 if bidirectional else 0,
+          _stream(stream))
+
+
+def channel_send_host(ch, from_block, src, nbytes, stream=None):
+    _call("channel_send_host", ch, from_block, int(src), nbytes, _stream(stream))
+
+
+def channel_recv_host(ch, at_block, dst, nbytes, stream=None):
+    _call("channel_recv_host", ch, at_block, int(dst), nbytes, _stream(stream))
+
+
+def channel_send_msg(ch, from_block, src, nbytes, stream=None):
+    _call("channel_send_msg", ch, from_block, int(src), nbytes, _stream(stream))
+
+
+def channel_recv_msg(ch, at_block, dst, nbytes, stream=None):
+    _call("channel_recv_msg", ch, at_block, int(dst), nbytes, _stream(stream))
 
 
 def channel_close(ch):

@@ -14,6 +14,7 @@
 // exactly once.
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 
 #include "runtime.h"
 
@@ -29,6 +30,15 @@ struct ChanCtr {
   uint64_t size[2][2];    // payload size of the message in slot [e][parity]
   uint32_t pp_arrive[2];  // ping-pong: CTA arrivals for messages to endpoint e
   uint32_t rdone[2];      // copy-out CTAs finished for the receive in flight at e
+  uint32_t bw_arrive[2];  // bandwidth test: CTA arrivals of windows sent to endpoint e
+  uint32_t bw_ack[2];     // bandwidth test: CTA arrivals of acknowledgements to e
+};
+
+// Host-side metadata message of the GPU Messaging form.
+struct MsgMeta {
+  const void* src;
+  size_t bytes;
+  uint64_t seq;
 };
 
 struct channel_s {
@@ -40,8 +50,12 @@ struct channel_s {
   void* slot[2][2] = {};   // [endpoint][parity]
   ChanCtr* ctr = nullptr;
   uint32_t* h_err = nullptr;
-  uint64_t sent[2] = {0, 0};   // messages sent BY endpoint e
-  uint64_t recvd[2] = {0, 0};  // messages received BY endpoint e
+  uint64_t sent[2] = {0, 0};   // device-channel messages sent BY endpoint e
+  uint64_t recvd[2] = {0, 0};  // device-channel messages received BY endpoint e
+                               // (the host-staged and Messaging forms keep out of these)
+  void* hstage[2] = {nullptr, nullptr};  // pinned host staging of the host-staged form, per receiver
+  std::deque<MsgMeta> mailbox[2];        // metadata messages waiting at endpoint e
+  uint64_t msg_seq[2] = {0, 0};
 };
 
 namespace {
@@ -139,6 +153,56 @@ __global__ void k_pingpong(ChanCtr* c, void* slot0, void* slot1, const void* src
           const uint32_t target = (uint32_t)G * (uint32_t)(r + 1);
           ok = wait_seq_ge(&c->pp_arrive[side], target, &c->err, wait_ns) ? 1 : 0;
         }
+        __syncthreads();
+        if (!ok) return;
+      }
+    }
+  }
+}
+
+// Plain multi-CTA device copy (the data movement of the GPU Messaging form).
+__global__ void k_msg_copy(void* dst, const void* src, size_t bytes) {
+  copy16(dst, src, bytes, (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
+}
+
+// OSU-style bandwidth test (Sec. 4.2.2) inside one cooperative launch.  CTAs
+// [0, G) are endpoint 0, [G, 2G) endpoint 1.  Each iteration the sender copies
+// `window` messages of `bytes` back to back into the peer's slot, then each of
+// its CTAs bumps the peer's arrival counter; the receiver waits for G arrivals
+// per iteration and (one-directional form) acknowledges with its own G
+// arrivals, which the sender waits for before the next window.  With
+// bidirectional set both endpoints send a window each iteration and the
+// arrivals double as acknowledgements.  All waits are bounded.
+__global__ void k_bandwidth(ChanCtr* c, void* slot0, void* slot1, const void* src0, const void* src1, size_t bytes,
+                            int window, int64_t iters, int G, int bidir, uint64_t wait_ns) {
+  const int side = blockIdx.x < (unsigned)G ? 0 : 1;
+  const int peer = 1 - side;
+  const int cta = side == 0 ? blockIdx.x : blockIdx.x - G;
+  const size_t tid = (size_t)cta * blockDim.x + threadIdx.x, nthr = (size_t)G * blockDim.x;
+  __shared__ int ok;
+  for (int64_t it = 0; it < iters; ++it) {
+    const uint32_t target = (uint32_t)G * (uint32_t)(it + 1);
+    if (side == 0 || bidir) {
+      for (int w = 0; w < window; ++w) copy16(peer == 1 ? slot1 : slot0, side == 0 ? src0 : src1, bytes, tid, nthr);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(&c->bw_arrive[peer], 1u);
+      }
+    }
+    if (side == 1 || bidir) {
+      if (threadIdx.x == 0) ok = wait_seq_ge(&c->bw_arrive[side], target, &c->err, wait_ns) ? 1 : 0;
+      __syncthreads();
+      if (!ok) return;
+    }
+    if (!bidir) {
+      if (side == 1) {
+        if (threadIdx.x == 0) {
+          __threadfence();
+          atomicAdd(&c->bw_ack[0], 1u);
+        }
+      } else {
+        if (threadIdx.x == 0) ok = wait_seq_ge(&c->bw_ack[0], target, &c->err, wait_ns) ? 1 : 0;
         __syncthreads();
         if (!ok) return;
       }
@@ -278,9 +342,87 @@ int channel_pingpong(channel_t* ch, size_t bytes, int64_t round_trips, int32_t c
   return JACOBI_OK;
 }
 
+int channel_send_host(channel_t* ch, int64_t from_block, const void* src, size_t bytes, void* stream) {
+  if (!ch || !src) return set_error(JACOBI_EINVAL, "null argument");
+  const int from = endpoint_of(ch, from_block);
+  if (from < 0) return set_error(JACOBI_EINVAL, "block is not an endpoint of the channel");
+  if (bytes > ch->max_bytes) return set_error(JACOBI_EINVAL, "message exceeds max_bytes");
+  const int to = 1 - from;
+  if (!ch->hstage[to]) JGB_CUDA(cudaMallocHost(&ch->hstage[to], ch->max_bytes));
+  // Device -> host into the staging buffer, then wait: only then may the host
+  // hand the message on.
+  JGB_CUDA(cudaMemcpyAsync(ch->hstage[to], src, bytes, cudaMemcpyDeviceToHost, S(stream)));
+  JGB_CUDA(cudaStreamSynchronize(S(stream)));
+  return JACOBI_OK;
+}
+
+int channel_recv_host(channel_t* ch, int64_t at_block, void* dst, size_t bytes, void* stream) {
+  if (!ch || !dst) return set_error(JACOBI_EINVAL, "null argument");
+  const int at = endpoint_of(ch, at_block);
+  if (at < 0) return set_error(JACOBI_EINVAL, "block is not an endpoint of the channel");
+  if (bytes > ch->max_bytes || !ch->hstage[at]) return set_error(JACOBI_EINVAL, "no host-staged message");
+  JGB_CUDA(cudaMemcpyAsync(dst, ch->hstage[at], bytes, cudaMemcpyHostToDevice, S(stream)));
+  JGB_CUDA(cudaStreamSynchronize(S(stream)));
+  return JACOBI_OK;
+}
+
+int channel_send_msg(channel_t* ch, int64_t from_block, const void* src, size_t bytes, void* stream) {
+  (void)stream;
+  if (!ch || !src) return set_error(JACOBI_EINVAL, "null argument");
+  const int from = endpoint_of(ch, from_block);
+  if (from < 0) return set_error(JACOBI_EINVAL, "block is not an endpoint of the channel");
+  if (bytes > ch->max_bytes) return set_error(JACOBI_EINVAL, "message exceeds max_bytes");
+  const int to = 1 - from;
+  ch->mailbox[to].push_back(MsgMeta{src, bytes, ch->msg_seq[to]++});
+  return JACOBI_OK;
+}
+
+int channel_recv_msg(channel_t* ch, int64_t at_block, void* dst, size_t bytes, void* stream) {
+  if (!ch || !dst) return set_error(JACOBI_EINVAL, "null argument");
+  const int at = endpoint_of(ch, at_block);
+  if (at < 0) return set_error(JACOBI_EINVAL, "block is not an endpoint of the channel");
+  if (ch->mailbox[at].empty()) return set_error(JACOBI_EAGAIN, "no metadata message has arrived yet");
+  const MsgMeta m = ch->mailbox[at].front();
+  if (m.bytes != bytes) return set_error(JACOBI_ESEQ, "message %llu has %zu bytes, receive expects %zu",
+                                         (unsigned long long)m.seq, m.bytes, bytes);
+  if ((uintptr_t)dst % 16 || (uintptr_t)m.src % 16) return set_error(JACOBI_EINVAL, "buffers must be 16-byte aligned");
+  ch->mailbox[at].pop_front();
+  // The receive is posted only now that the metadata is here: issue the copy
+  // and wait for its completion.
+  k_msg_copy<<<copy_ctas(bytes), kChanThreads, 0, S(stream)>>>(dst, m.src, bytes);
+  JGB_CUDA(cudaGetLastError());
+  JGB_CUDA(cudaStreamSynchronize(S(stream)));
+  return JACOBI_OK;
+}
+
+int channel_bandwidth(channel_t* ch, size_t bytes, int32_t window, int64_t iterations, int32_t ctas_per_side,
+                      int32_t bidirectional, void* stream) {
+  if (!ch || window < 1 || iterations < 0 || ctas_per_side < 1) return set_error(JACOBI_EINVAL, "bad arguments");
+  if (bytes > ch->max_bytes) return set_error(JACOBI_EINVAL, "message exceeds max_bytes");
+  int dev = 0, sms = 0, per_sm = 0;
+  JGB_CUDA(cudaGetDevice(&dev));
+  JGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  JGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bandwidth, kChanThreads, 0));
+  if (2 * ctas_per_side > per_sm * sms) return set_error(JACOBI_EINVAL, "too many CTAs for a co-resident launch");
+  const cudaStream_t s = S(stream);
+  JGB_CUDA(cudaMemsetAsync(ch->ctr->bw_arrive, 0, sizeof(ch->ctr->bw_arrive) + sizeof(ch->ctr->bw_ack), s));
+  void* slot0 = ch->slot[0][0];
+  void* slot1 = ch->slot[1][0];
+  const void* src0 = ch->slot[0][1];
+  const void* src1 = ch->slot[1][1];
+  ChanCtr* c = ch->ctr;
+  int G = ctas_per_side, W = window, bidir = bidirectional ? 1 : 0;
+  uint64_t wn = ch->h->wait_ns;
+  void* args[] = {&c, &slot0, &slot1, (void*)&src0, (void*)&src1, &bytes, &W, &iterations, &G, &bidir, &wn};
+  JGB_CUDA(cudaLaunchCooperativeKernel((const void*)k_bandwidth, dim3(2 * G), dim3(kChanThreads), args, 0, s));
+  return JACOBI_OK;
+}
+
 int channel_close(channel_t* ch) {
   if (!ch) return JACOBI_OK;
   cudaDeviceSynchronize();
+  for (int e = 0; e < 2; ++e)
+    if (ch->hstage[e]) cudaFreeHost(ch->hstage[e]);
   jacobi_t* h = ch->h;
   for (size_t q = 0; q < h->channels.size(); ++q)
     if (h->channels[q] == ch) {

@@ -156,3 +156,55 @@ def test_pingpong_runs_and_delivers(solver, nbytes, ctas):
         assert torch.equal(_view(jg.channel_slot(ch, 0, 0), nbytes), b)
     finally:
         jg.channel_close(ch)
+
+
+def test_host_staged_and_messaging_forms(solver):
+    ch = jg.channel_open(solver.h, 30, 0, 1, 1 << 20)
+    try:
+        for k, n in enumerate([16, 4096, 1 << 20]):
+            src = _payload(n, 200 + k)
+            dst = torch.zeros(n, dtype=torch.uint8, device="cuda")
+            jg.channel_send_host(ch, 0, src.data_ptr(), n)
+            jg.channel_recv_host(ch, 1, dst.data_ptr(), n)
+            assert torch.equal(dst, src)
+            dst.zero_()
+            jg.channel_send_msg(ch, 1, src.data_ptr(), n)
+            jg.channel_recv_msg(ch, 0, dst.data_ptr(), n)
+            assert torch.equal(dst, src)
+        # the receive can only be posted once the metadata message is there
+        d = torch.zeros(256, dtype=torch.uint8, device="cuda")
+        with pytest.raises(jg.JacobiError) as e:
+            jg.channel_recv_msg(ch, 1, d.data_ptr(), 64)
+        assert e.value.code == jg.JACOBI_EAGAIN
+        m = _payload(64, 7)
+        jg.channel_send_msg(ch, 0, m.data_ptr(), 64)
+        with pytest.raises(jg.JacobiError) as e:
+            jg.channel_recv_msg(ch, 1, d.data_ptr(), 32)
+        assert e.value.code == jg.JACOBI_ESEQ
+        # the comparison forms leave the device channel's sequence numbers alone
+        for k in range(5):
+            src = _payload(256, 300 + k)
+            jg.channel_send(ch, k % 2, src.data_ptr(), 256)
+            jg.channel_recv(ch, 1 - k % 2, d.data_ptr(), 256)
+            jg.channel_sync(ch)
+            assert torch.equal(d, src)
+    finally:
+        jg.channel_close(ch)
+
+
+@pytest.mark.parametrize("bidir", [False, True])
+def test_bandwidth_window_runs_and_delivers(solver, bidir):
+    n = 1 << 20
+    ch = jg.channel_open(solver.h, 31, 2, 3, n)
+    try:
+        a, b = _payload(n, 11), _payload(n, 12)
+        _view(jg.channel_slot(ch, 2, 1), n).copy_(a)
+        _view(jg.channel_slot(ch, 3, 1), n).copy_(b)
+        torch.cuda.synchronize()
+        jg.channel_bandwidth(ch, n, 8, 5, 8, bidir)
+        jg.channel_sync(ch)
+        assert torch.equal(_view(jg.channel_slot(ch, 3, 0), n), a)
+        if bidir:
+            assert torch.equal(_view(jg.channel_slot(ch, 2, 0), n), b)
+    finally:
+        jg.channel_close(ch)

@@ -133,6 +133,10 @@ WORKLOADS = {
     "jacobi3d-fp64-512c-8x8x8": dict(grid=(512, 512, 512), split=("count", (8, 8, 8)), dtype="f64",
                                      bc="uniform", bc_seed=1, interior="zero", interior_seed=0,
                                      iters=1000),
+    # One GPU's share of the paper's weak-scaling base problem (1536^3 doubles on
+    # a node of six GPUs, Sec. 4.3), overdecomposed into 64^3 blocks.
+    "jacobi3d-fp64-1536x768x512": dict(grid=(1536, 768, 512), split=("shape", (64, 64, 64)), dtype="f64",
+                                       bc="uniform", bc_seed=1, interior="zero", interior_seed=0, iters=100),
     # 256^3 versions of the two above: small cases for profiler captures
     # (two 134 MB FP64 state copies, still larger than L2).
     "jacobi3d-fp64-256c-4x4x4": dict(grid=(256, 256, 256), split=("count", (4, 4, 4)), dtype="f64",

@@ -158,6 +158,9 @@ BATCHED = {
                                      interior="zero", iters=500),
     "jacobi3d-batched256-fp64": dict(n_grids=256, sides_seed=2, block=(32, 32, 32), dtype="f64", bc="uniform",
                                      interior="zero", iters=500),
+    # the first 32 grids of the batch: a small case for profiler captures
+    "jacobi3d-batched32-fp32": dict(n_grids=32, sides_seed=2, block=(32, 32, 32), dtype="f32", bc="uniform",
+                                    interior="zero", iters=20),
 }
 
 

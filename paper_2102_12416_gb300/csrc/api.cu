@@ -49,35 +49,39 @@ static int axis_split(int64_t n, int32_t mode, int64_t param, std::vector<std::p
   return JACOBI_OK;
 }
 
-// Rows per thread for the plane-streaming path, or 0 when the block shape does
-// not fit it.  Rows must split into 16-byte vectors (which also keeps every
-// bulk copy 16-byte aligned); one CTA of kThreads threads covers a window of
-// `chunk` rows (a multiple of both the rows per thread and the vector width),
-// so a plane is split into ceil(ny / chunk) windows; a ring stage of a window
-// must fit shared memory four times over.
-static int stream_rows(int64_t nx, int64_t ny, size_t elem, uint32_t* stage_bytes, int64_t* chunk) {
+// Rows per thread and consumer warps for the plane-streaming path, or 0 when
+// the block shape does not fit it.  Rows must split into 16-byte vectors
+// (which also keeps every bulk copy 16-byte aligned).  Each thread computes RY
+// rows (4 when ny allows it) of one vector column; a CTA of CW consumer warps
+// (2, 4 or 8: the smallest that covers the plane) covers a window of `chunk`
+// rows (a multiple of RY and of the vector width), so large planes are split
+// into ceil(ny / chunk) windows and small ones run in small CTAs, several per
+// SM.  A ring stage of a window must fit shared memory four times over.
+static int stream_rows(int64_t nx, int64_t ny, size_t elem, uint32_t* stage_bytes, int64_t* chunk, int* cw_out) {
   const int64_t vec = 16 / (int64_t)elem;
   if (nx % vec || ny % vec) return 0;
   const int64_t txv = nx / vec;
   if (txv > kThreads) return 0;
-  const int64_t tpr = kThreads / txv;
-  int ry = 0;
+  int ry = 4;
+  while (ry > 1 && (ny % ry)) ry /= 2;
+  const int64_t L = std::max<int64_t>(ry, vec);
+  int cw = 8;
   int64_t ch = 0;
-  for (int r = 1; r <= 4; r *= 2) {
-    if (ny % r) break;
-    const int64_t L = std::max<int64_t>(r, vec);
-    const int64_t c = tpr * r / L * L;
-    if (c <= 0) continue;
-    ry = r;
-    ch = c;
-    if (c >= ny) break;
+  if (ry == 4) {
+    for (int c = 2; c <= 8; c *= 2)
+      if (txv * ((ny + ry - 1) / ry) <= 32 * c) {
+        cw = c;
+        break;
+      }
   }
-  if (!ry) return 0;
+  ch = (32 * cw / txv) * ry / L * L;
+  if (ch <= 0) return 0;
   ch = std::min(ch, ny);
   const uint64_t stage = ((uint64_t)((ch + 2) * nx + 2 * ch + 2 * nx) * elem + 127) / 128 * 128;
   if (128 + 4 * stage > (uint64_t)kMaxStepSmem) return 0;
   *stage_bytes = (uint32_t)stage;
   *chunk = ch;
+  *cw_out = cw;
   return ry;
 }
 
@@ -154,15 +158,17 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
   // the largest power-of-two fraction of the tallest block that still gives
   // at least `target_items` items (or 2 planes), so small problems still
   // spread over many CTAs while large ones stream whole blocks.
-  std::vector<int> rows(P->blocks.size());
+  std::vector<int> rows(P->blocks.size()), warps(P->blocks.size());
   std::vector<int64_t> chunks(P->blocks.size());
   int64_t units = 0, maxz = 0;
   for (size_t b = 0; b < P->blocks.size(); ++b) {
     const BlockHost& B = P->blocks[b];
     uint32_t sb = 0;
     int64_t ch = 0;
-    const int ry = stream_rows(B.extent[0], B.extent[1], P->elem, &sb, &ch);
+    int cw = 8;
+    const int ry = stream_rows(B.extent[0], B.extent[1], P->elem, &sb, &ch, &cw);
     rows[b] = ry;
+    warps[b] = cw;
     chunks[b] = ch;
     if (ry) P->max_stage = std::max(P->max_stage, sb);
     units += ry ? (B.extent[1] + ch - 1) / ch : ((B.extent[0] + TX - 1) / TX) * ((B.extent[1] + TY - 1) / TY);
@@ -186,7 +192,7 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
           for (int64_t ya = 0; ya < B.extent[1]; ya += chunks[b]) {
             w.slot = (int32_t)P->items.size();
             w.x0 = -1;
-            w.y0 = (int16_t)ry;
+            w.y0 = (int16_t)(ry + 16 * warps[b]);
             w.ya = (int16_t)ya;
             w.yb = (int16_t)std::min(B.extent[1], ya + chunks[b]);
             P->items.push_back(w);

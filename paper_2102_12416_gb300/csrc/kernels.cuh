@@ -26,11 +26,18 @@ struct BlockGeom {
 // 227 KB per CTA, minus room for the kernels' static shared memory).
 constexpr int kMaxStepSmem = 227 * 1024 - 1024;  // 1 KB left for static shared memory
 
-// Item kinds of a step launch: 0 = tiles, 1..3 = plane streaming with 1, 2,
-// 4 rows per thread.  Each kind runs its own kernel variant.
-constexpr int kItemKinds = 4;
+// A plane-streaming item encodes its rows per thread RY and its consumer warps
+// CW in y0 = RY + 16 * CW.  Item kinds of a step launch: 0 = tiles; 1, 2, 3 =
+// streaming with RY = 1, 2, 4 and CW = 8; 4 = RY 4, CW 4; 5 = RY 4, CW 2.
+// Each kind runs its own kernel variant.
+constexpr int kItemKinds = 6;
+__host__ __device__ inline int item_rows(const WorkItem& w) { return w.y0 & 15; }
+__host__ __device__ inline int item_warps(const WorkItem& w) { return w.y0 >> 4; }
 __host__ __device__ inline int item_kind(const WorkItem& w) {
-  return w.x0 >= 0 ? 0 : (w.y0 == 1 ? 1 : w.y0 == 2 ? 2 : 3);
+  if (w.x0 >= 0) return 0;
+  const int ry = item_rows(w), cw = item_warps(w);
+  if (cw == 8) return ry == 1 ? 1 : ry == 2 ? 2 : 3;
+  return cw == 4 ? 4 : 5;
 }
 
 struct StepLaunch {

@@ -235,14 +235,42 @@ __device__ __forceinline__ void issue_plane(const BlockDev& B, int p, int z0, in
   if (gyp) bulk_g2s(dst + L.o_yp, (const T*)B.recv[YP][p] + (int64_t)kk * nx, L.yg, bar);
 }
 
+// What a consumer thread needs from its block, read once per work item into
+// registers (the block table lives in global memory and the sweep stores
+// through plain pointers, so reading it in the loop would force reloads).
+template <typename T>
+struct PlaneView {
+  int nx, ny, nz, pn;      // extents; parity of the new iterate
+  int64_t pitch;
+  T* V;                    // new iterate
+  const BlockDev* B;       // for the send pointers, read by edge threads only
+};
+template <typename T>
+__device__ __forceinline__ PlaneView<T> plane_view(const BlockDev& B, int p) {
+  PlaneView<T> v;
+  v.nx = B.nx;
+  v.ny = B.ny;
+  v.nz = B.nz;
+  v.pn = p ^ 1;
+  v.pitch = B.plane_pitch;
+  v.V = (T*)B.u[p ^ 1];
+  v.B = &B;
+  return v;
+}
+// Neighbour receive slot of face f for the new iterate (read-only path).
+template <typename T>
+__device__ __forceinline__ T* send_slot(const PlaneView<T>& O, int f) {
+  return (T*)__ldg((const unsigned long long*)&O.B->send[f][O.pn]);
+}
+
 // Compute plane k of rows [j0, j0 + RY) (inside the window [ya, yb)) from the
 // stages holding planes k - 1, k, k + 1.  tx = vector column.
 template <typename T, int RY, int MODE, bool EMU>
-__device__ __forceinline__ double stream_plane(const BlockDev& B, int p, int k, int ya, const StageLayout& L,
+__device__ __forceinline__ double stream_plane(const PlaneView<T>& O, int k, int ya, const StageLayout& L,
                                                const unsigned char* sm, const unsigned char* sc,
                                                const unsigned char* sp, int tx, int j0) {
   constexpr int VEC = V16<T>::N;
-  const int nx = B.nx, ny = B.ny, nz = B.nz;
+  const int nx = O.nx, ny = O.ny, nz = O.nz;
   const int i0 = tx * VEC;
   const T* Pm = (const T*)sm - L.ra * nx;  // row j of a plane at P + j * nx
   const T* Pc = (const T*)sc - L.ra * nx;
@@ -251,7 +279,7 @@ __device__ __forceinline__ double stream_plane(const BlockDev& B, int p, int k, 
   const T* Gxp = (const T*)(sc + L.o_xp) - ya;
   const T* Gym = (const T*)(sc + L.o_ym);
   const T* Gyp = (const T*)(sc + L.o_yp);
-  T* __restrict__ V = (T*)B.u[p ^ 1] + (int64_t)k * B.plane_pitch;
+  T* __restrict__ V = O.V + (int64_t)k * O.pitch;
 
   T c[RY][VEC];
 #pragma unroll
@@ -283,27 +311,27 @@ __device__ __forceinline__ double stream_plane(const BlockDev& B, int p, int k, 
       V16<T>::store(V + j * nx + i0, v);
       if (MODE & kPack) {
         if (i0 == 0) {
-          T* d = (T*)B.send[XM][p ^ 1];
+          T* d = send_slot(O, XM);
           if (d) d[(int64_t)k * ny + j] = v[0];
         }
         if (i0 + VEC == nx) {
-          T* d = (T*)B.send[XP][p ^ 1];
+          T* d = send_slot(O, XP);
           if (d) d[(int64_t)k * ny + j] = v[VEC - 1];
         }
         if (j == 0) {
-          T* d = (T*)B.send[YM][p ^ 1];
+          T* d = send_slot(O, YM);
           if (d) V16<T>::store(d + (int64_t)k * nx + i0, v);
         }
         if (j == ny - 1) {
-          T* d = (T*)B.send[YP][p ^ 1];
+          T* d = send_slot(O, YP);
           if (d) V16<T>::store(d + (int64_t)k * nx + i0, v);
         }
         if (k == 0) {
-          T* d = (T*)B.send[ZM][p ^ 1];
+          T* d = send_slot(O, ZM);
           if (d) V16<T>::store(d + j * nx + i0, v);
         }
         if (k == nz - 1) {
-          T* d = (T*)B.send[ZP][p ^ 1];
+          T* d = send_slot(O, ZP);
           if (d) V16<T>::store(d + j * nx + i0, v);
         }
       }
@@ -326,6 +354,7 @@ __device__ double stream_item(const BlockDev& B, int p, const WorkItem& w, Ring&
   const bool active = j0 < w.yb;
   const int S = ring.S;
   const StageLayout L = stage_layout<T>(B, w.ya, w.yb);
+  const PlaneView<T> O = plane_view<T>(B, p);
   const int nplanes = w.z1 - w.z0 + 2;
   auto issue = [&](int q) {
     const int st = q % S;
@@ -362,9 +391,9 @@ __device__ double stream_item(const BlockDev& B, int p, const WorkItem& w, Ring&
       const unsigned char* sc = ring.stages + (size_t)(q % S) * L.bytes;
       const unsigned char* sp = ring.stages + (size_t)((q + 1) % S) * L.bytes;
       if (sizeof(T) == 8 && emu)
-        acc += stream_plane<T, RY, MODE, true>(B, p, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
+        acc += stream_plane<T, RY, MODE, true>(O, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
       else
-        acc += stream_plane<T, RY, MODE, false>(B, p, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
+        acc += stream_plane<T, RY, MODE, false>(O, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
     }
   }
   ok = __syncthreads_and(good) != 0;
@@ -389,7 +418,7 @@ __device__ double run_item(const BlockDev& B, int p, const WorkItem& w, Ring& ri
                            uint64_t wait_ns, bool emu, bool& ok) {
   ok = true;
   if (w.x0 >= 0) return tile_sweep<T, MODE>(B, p, w.x0, w.y0, w.z0, w.z1, threadIdx.x % TX, threadIdx.x / TX);
-  switch (w.y0) {
+  switch (item_rows(w)) {
     case 1: return stream_item<T, 1, MODE>(B, p, w, ring, err, wait_ns, emu, ok);
     case 2: return stream_item<T, 2, MODE>(B, p, w, ring, err, wait_ns, emu, ok);
     default: return stream_item<T, 4, MODE>(B, p, w, ring, err, wait_ns, emu, ok);
@@ -437,15 +466,18 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
 // the planes it needs, computes, and releases the stage of plane q - 1 after
 // computing plane q, its last use).  There is no CTA-wide barrier inside the
 // plane loop, so consumer warps drift freely within the ring.
-constexpr int kConsumerWarps = kThreads / 32;
-constexpr int kStreamThreads = kThreads + 32;
+// CW consumer warps (2, 4 or 8) plus the producer warp; small planes use
+// small CTAs so that every consumer thread still computes RY = 4 rows.  The
+// register cap (72 per thread) sets the minimum CTAs per SM.
+template <int CW> struct StreamShape {
+  static constexpr int threads = 32 * CW + 32;
+  static constexpr int min_blocks = 65536 / (threads * 72);
+};
 
-template <typename T> struct StreamOcc;
-template <> struct StreamOcc<float> { static constexpr int min_blocks = 3; };
-template <> struct StreamOcc<double> { static constexpr int min_blocks = 3; };
-
-template <typename T, int RY, int MODE>
-__global__ void __launch_bounds__(kStreamThreads, StreamOcc<T>::min_blocks) k_stream(StepLaunch a) {
+template <typename T, int RY, int CW, int MODE>
+__global__ void __launch_bounds__(StreamShape<CW>::threads, StreamShape<CW>::min_blocks) k_stream(StepLaunch a) {
+  constexpr int kConsumerWarps = CW;
+  constexpr int kStreamThreads = StreamShape<CW>::threads;
   constexpr int VEC = V16<T>::N;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = (uint64_t*)smem;
@@ -491,7 +523,8 @@ __global__ void __launch_bounds__(kStreamThreads, StreamOcc<T>::min_blocks) k_st
   } else {
     // ---- consumers ----
     const bool emu = sizeof(T) == 8 && a.emu && a.norms && a.norms[B.grid].emu_bad == 0u;
-    const int txv = B.nx / VEC;
+    const PlaneView<T> O = plane_view<T>(B, p);
+    const int txv = O.nx / VEC;
     const int tx = tid % txv, j0 = w.ya + (tid / txv) * RY;
     const bool active = j0 < w.yb;
     bool good = true;
@@ -508,9 +541,9 @@ __global__ void __launch_bounds__(kStreamThreads, StreamOcc<T>::min_blocks) k_st
         const unsigned char* sc = stages + (size_t)(q % S) * L.bytes;
         const unsigned char* sp = stages + (size_t)((q + 1) % S) * L.bytes;
         if (sizeof(T) == 8 && emu)
-          acc += stream_plane<T, RY, MODE, true>(B, p, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
+          acc += stream_plane<T, RY, MODE, true>(O, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
         else
-          acc += stream_plane<T, RY, MODE, false>(B, p, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
+          acc += stream_plane<T, RY, MODE, false>(O, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(empty + (q - 1) % S);
@@ -592,12 +625,12 @@ cudaError_t set_smem_attr(K kernel, bool& done) {
   return e;
 }
 
-template <typename T, int RY, int MODE>
+template <typename T, int RY, int CW, int MODE>
 cudaError_t launch_stream(const StepLaunch& a, cudaStream_t s) {
   static bool done = false;
-  cudaError_t e = set_smem_attr(k_stream<T, RY, MODE>, done);
+  cudaError_t e = set_smem_attr(k_stream<T, RY, CW, MODE>, done);
   if (e != cudaSuccess) return e;
-  k_stream<T, RY, MODE><<<a.n_items, kStreamThreads, a.smem, s>>>(a);
+  k_stream<T, RY, CW, MODE><<<a.n_items, StreamShape<CW>::threads, a.smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -611,9 +644,11 @@ cudaError_t launch_kinds(const StepLaunch& a, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
     switch (kind) {
       case 0: k_tiles<T, MODE><<<b.n_items, kThreads, 0, s>>>(b); e = cudaGetLastError(); break;
-      case 1: e = launch_stream<T, 1, MODE>(b, s); break;
-      case 2: e = launch_stream<T, 2, MODE>(b, s); break;
-      default: e = launch_stream<T, 4, MODE>(b, s); break;
+      case 1: e = launch_stream<T, 1, 8, MODE>(b, s); break;
+      case 2: e = launch_stream<T, 2, 8, MODE>(b, s); break;
+      case 3: e = launch_stream<T, 4, 8, MODE>(b, s); break;
+      case 4: e = launch_stream<T, 4, 4, MODE>(b, s); break;
+      default: e = launch_stream<T, 4, 2, MODE>(b, s); break;
     }
     if (e != cudaSuccess) return e;
   }

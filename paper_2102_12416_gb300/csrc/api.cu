@@ -49,43 +49,40 @@ static int axis_split(int64_t n, int32_t mode, int64_t param, std::vector<std::p
   return JACOBI_OK;
 }
 
-// Rows per thread and consumer warps for the plane-streaming path, or 0 when
-// the block shape does not fit it.  Rows must split into 16-byte vectors
-// (which also keeps every bulk copy 16-byte aligned).  Each thread computes RY
-// rows (4 when ny allows it) of one vector column; a CTA of CW consumer warps
-// (2, 4 or 8: the smallest that covers the plane) covers a window of `chunk`
-// rows (a multiple of RY and of the vector width), so large planes are split
-// into ceil(ny / chunk) windows and small ones run in small CTAs, several per
+// Consumer warps per CTA for the plane-streaming path, or 0 when a padded
+// row is wider than one CTA can cover (more than 256 vectors of 16 bytes).
+// Each consumer thread computes 4 rows of one vector column; a CTA of CW
+// consumer warps (2, 4 or 8: the smallest that covers the padded plane)
+// covers a window of `chunk` rows (a multiple of 4), so large planes are split
+// into ceil(ry / chunk) windows and small ones run in small CTAs, several per
 // SM.  A ring stage of a window must fit shared memory four times over.
-static int stream_rows(int64_t nx, int64_t ny, size_t elem, uint32_t* stage_bytes, int64_t* chunk, int* cw_out) {
-  const int64_t vec = 16 / (int64_t)elem;
-  if (nx % vec || ny % vec) return 0;
-  const int64_t txv = nx / vec;
+static int stream_shape(int64_t rx, int64_t ry, size_t elem, uint32_t* stage_bytes, int64_t* chunk) {
+  const int64_t txv = rx / (16 / (int64_t)elem);
   if (txv > kThreads) return 0;
-  int ry = 4;
-  while (ry > 1 && (ny % ry)) ry /= 2;
-  const int64_t L = std::max<int64_t>(ry, vec);
   int cw = 8;
-  int64_t ch = 0;
-  if (ry == 4) {
-    for (int c = 2; c <= 8; c *= 2)
-      if (txv * ((ny + ry - 1) / ry) <= 32 * c) {
-        cw = c;
-        break;
-      }
-  }
-  ch = (32 * cw / txv) * ry / L * L;
+  for (int c = 2; c <= 8; c *= 2)
+    if (txv * (ry / 4) <= 32 * c) {
+      cw = c;
+      break;
+    }
+  int64_t ch = (32 * cw / txv) * 4;
   if (ch <= 0) return 0;
-  ch = std::min(ch, ny);
-  const uint64_t stage = ((uint64_t)((ch + 2) * nx + 2 * ch + 2 * nx) * elem + 127) / 128 * 128;
+  ch = std::min(ch, ry);
+  const uint64_t stage = ((uint64_t)((ch + 2) * rx + 2 * ch + 2 * rx) * elem + 127) / 128 * 128;
   if (128 + 4 * stage > (uint64_t)kMaxStepSmem) return 0;
   *stage_bytes = (uint32_t)stage;
   *chunk = ch;
-  *cw_out = cw;
-  return ry;
+  return cw;
 }
 
+// Entries of the padded receive slot of face f (see BlockDev), and of the
+// face itself.
 static int64_t face_elems_host(const BlockHost& b, int f) {
+  if (f < 2) return b.ry * b.extent[2];
+  if (f < 4) return b.rx * b.extent[2];
+  return b.rx * b.ry;
+}
+static int64_t face_points_host(const BlockHost& b, int f) {
   if (f < 2) return b.extent[1] * b.extent[2];
   if (f < 4) return b.extent[0] * b.extent[2];
   return b.extent[0] * b.extent[1];
@@ -158,20 +155,21 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
   // the largest power-of-two fraction of the tallest block that still gives
   // at least `target_items` items (or 2 planes), so small problems still
   // spread over many CTAs while large ones stream whole blocks.
-  std::vector<int> rows(P->blocks.size()), warps(P->blocks.size());
+  std::vector<int> warps(P->blocks.size());
   std::vector<int64_t> chunks(P->blocks.size());
   int64_t units = 0, maxz = 0;
+  const int64_t vec = 16 / (int64_t)P->elem;
   for (size_t b = 0; b < P->blocks.size(); ++b) {
-    const BlockHost& B = P->blocks[b];
+    BlockHost& B = P->blocks[b];
+    B.rx = (B.extent[0] + vec - 1) / vec * vec;
+    B.ry = (B.extent[1] + 3) / 4 * 4;
     uint32_t sb = 0;
     int64_t ch = 0;
-    int cw = 8;
-    const int ry = stream_rows(B.extent[0], B.extent[1], P->elem, &sb, &ch, &cw);
-    rows[b] = ry;
+    const int cw = stream_shape(B.rx, B.ry, P->elem, &sb, &ch);
     warps[b] = cw;
     chunks[b] = ch;
-    if (ry) P->max_stage = std::max(P->max_stage, sb);
-    units += ry ? (B.extent[1] + ch - 1) / ch : ((B.extent[0] + TX - 1) / TX) * ((B.extent[1] + TY - 1) / TY);
+    if (cw) P->max_stage = std::max(P->max_stage, sb);
+    units += cw ? (B.ry + ch - 1) / ch : ((B.extent[0] + TX - 1) / TX) * ((B.extent[1] + TY - 1) / TY);
     maxz = std::max(maxz, B.extent[2]);
   }
   int64_t zc = maxz;
@@ -180,7 +178,7 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
     G.item_begin = (int64_t)P->items.size();
     for (int64_t b = G.block_begin; b < G.block_end; ++b) {
       BlockHost& B = P->blocks[b];
-      const int ry = rows[b];
+      const int cw = warps[b];
       B.item_begin = (int64_t)P->items.size();
       for (int64_t z0 = 0; z0 < B.extent[2]; z0 += zc) {
         WorkItem w;
@@ -188,13 +186,13 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
         w.z0 = (int16_t)z0;
         w.z1 = (int16_t)std::min(B.extent[2], z0 + zc);
         w.ya = w.yb = 0;
-        if (ry) {
-          for (int64_t ya = 0; ya < B.extent[1]; ya += chunks[b]) {
+        if (cw) {
+          for (int64_t ya = 0; ya < B.ry; ya += chunks[b]) {
             w.slot = (int32_t)P->items.size();
             w.x0 = -1;
-            w.y0 = (int16_t)(ry + 16 * warps[b]);
+            w.y0 = (int16_t)(cw | (B.rx != B.extent[0] || B.ry != B.extent[1] ? kItemRagged : 0));
             w.ya = (int16_t)ya;
-            w.yb = (int16_t)std::min(B.extent[1], ya + chunks[b]);
+            w.yb = (int16_t)std::min(B.ry, ya + chunks[b]);
             P->items.push_back(w);
           }
           continue;
@@ -232,7 +230,7 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
   P->off_pblock_ids = take(nb * sizeof(int32_t));
   const size_t per16 = 32;  // plane pitch rounded to 32 elements
   for (auto& B : P->blocks) {
-    B.pitch = (int64_t)align_up((size_t)(B.extent[0] * B.extent[1]), per16);
+    B.pitch = (int64_t)align_up((size_t)(B.rx * B.ry), per16);
     const size_t sb = (size_t)B.pitch * B.extent[2] * P->elem;
     B.u_off[0] = take(sb);
     B.u_off[1] = take(sb);
@@ -243,7 +241,7 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
       if (B.nbr[f] >= 0) {
         B.recv_off[f][0] = take(fb);
         B.recv_off[f][1] = take(fb);
-        P->halo_elems += face_elems_host(B, f);
+        P->halo_elems += face_points_host(B, f);
       } else {
         B.recv_off[f][0] = B.recv_off[f][1] = take(fb);
       }
@@ -281,6 +279,8 @@ void fill_block_tables(const Plan& P, char* ws, int64_t base, int32_t grid_overr
     D.nz = (int32_t)B.extent[2];
     D.grid = grid_override >= 0 ? grid_override : (int32_t)B.grid;
     D.plane_pitch = B.pitch;
+    D.rx = (int32_t)B.rx;
+    D.ry = (int32_t)B.ry;
     geo[b] = BlockGeom{(int32_t)B.origin[0], (int32_t)B.origin[1], (int32_t)B.origin[2], D.grid};
   }
 }
@@ -425,7 +425,7 @@ int step_fused_direct(jacobi_t* h, int64_t it0, int64_t n, cudaStream_t s) {
   StepLaunch a = step_args(h, 0, false);
   for (int64_t t = 0; t < n; ++t) {
     a.it = it0 + t;
-    JGB_CUDA(launch_step(a, kWrite | kPack, s));
+    JGB_CUDA(launch_step(a, kWrite | kPack, s, &h->fork));
   }
   return JACOBI_OK;
 }
@@ -450,7 +450,7 @@ int step_graph(jacobi_t* h, int64_t it0, int64_t n, cudaStream_t s) {
         StepLaunch a = step_args(h, 0, false);
         for (int64_t t = 0; t < K && e == cudaSuccess; ++t) {
           a.it = t;
-          e = launch_step(a, kWrite | kPack, cs);
+          e = launch_step(a, kWrite | kPack, cs, &h->fork);
         }
         cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         if (e == cudaSuccess) e = e2;
@@ -504,7 +504,7 @@ int step_explicit(jacobi_t* h, int64_t it0, int64_t n, cudaStream_t s) {
   const int32_t nb = (int32_t)h->plan.blocks.size();
   for (int64_t t = 0; t < n; ++t) {
     a.it = it0 + t;
-    JGB_CUDA(launch_step(a, kWrite, s));
+    JGB_CUDA(launch_step(a, kWrite, s, &h->fork));
     JGB_CUDA(launch_pack_faces(h->d_blocks, nb, h->d_stage_tab, h->d_grids, a.it, h->plan.dtype, s));
     JGB_CUDA(launch_copy_faces(h->d_blocks, nb, h->d_stage_tab, h->d_grids, a.it, h->plan.dtype, s));
   }
@@ -541,7 +541,7 @@ int step_with_residual(jacobi_t* h, cudaStream_t s) {
     if (rc) return rc;
   } else {
     StepLaunch a = step_args(h, h->iter, false);
-    JGB_CUDA(launch_step(a, kWrite | kPack | kResid, s));
+    JGB_CUDA(launch_step(a, kWrite | kPack | kResid, s, &h->fork));
     if (h->path == JACOBI_PATH_EXPLICIT) {
       // the fused pack already delivered the faces; nothing else to move
     }
@@ -555,7 +555,7 @@ int residual_only(jacobi_t* h, cudaStream_t s) {
   int rc = refresh_active(h, s);
   if (rc) return rc;
   StepLaunch a = step_args(h, h->iter, false);
-  JGB_CUDA(launch_step(a, kResid, s));
+  JGB_CUDA(launch_step(a, kResid, s, &h->fork));
   JGB_CUDA(launch_reduce(h->d_grids, h->d_norms, h->d_gids, (int32_t)h->plan.grids.size(), h->d_partials, 0, s));
   return JACOBI_OK;
 }
@@ -685,6 +685,7 @@ int jacobi_create_batch(int64_t n_grids, const jacobi_dim3* grids, const jacobi_
   }
   const cudaStream_t s = S(stream);
   auto fail = [&](int code) {
+    kind_fork_destroy(&h->fork);
     if (h->own_ws && h->ws) cudaFree(h->ws);
     if (h->h_grids) cudaFreeHost(h->h_grids);
     if (h->h_norms) cudaFreeHost(h->h_norms);
@@ -694,6 +695,8 @@ int jacobi_create_batch(int64_t n_grids, const jacobi_dim3* grids, const jacobi_
   };
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) return fail(set_error(JACOBI_ECUDA, "no CUDA device: %s", cudaGetErrorString(e)));
+  e = kind_fork_create(&h->fork);
+  if (e != cudaSuccess) return fail(set_error(JACOBI_ECUDA, "stream creation failed: %s", cudaGetErrorString(e)));
   if (workspace) {
     if (ws_bytes < h->plan.bytes)
       return fail(set_error(JACOBI_ENOMEM, "workspace too small: %zu < %zu bytes", ws_bytes, h->plan.bytes));
@@ -740,6 +743,10 @@ int jacobi_create_batch(int64_t n_grids, const jacobi_dim3* grids, const jacobi_
     if (v >= 3 && v <= 8) h->stages = v;
   }
   if (128 + h->stages * (int64_t)P.max_stage > kMaxStepSmem) h->stages = 3;
+  // Zero the workspace so the padding of every row, plane and slot starts
+  // finite (and inside the FP64 integer adder's domain).
+  e = cudaMemsetAsync(h->ws, 0, P.bytes, s);
+  if (e != cudaSuccess) return fail(set_error(JACOBI_ECUDA, "workspace clear failed: %s", cudaGetErrorString(e)));
   rc = upload_tables(h, s);
   if (rc) return fail(rc);
   e = launch_init(h->d_blocks, h->d_geom, (int32_t)P.blocks.size(), h->d_inits, P.dtype, s);
@@ -762,6 +769,7 @@ int jacobi_destroy(jacobi_t* h) {
   cudaDeviceSynchronize();
   for (channel_s* c : std::vector<channel_s*>(h->channels)) channel_close(c);
   if (h->graph) cudaGraphExecDestroy(h->graph);
+  kind_fork_destroy(&h->fork);
   if (h->stage) cudaFree(h->stage);
   if (h->own_ws && h->ws) cudaFree(h->ws);
   if (h->h_grids) cudaFreeHost(h->h_grids);
@@ -1139,8 +1147,14 @@ int jacobi_read_face(jacobi_t* h, int64_t block, int32_t face, void* dst, void* 
     return set_error(JACOBI_EINVAL, "bad arguments to jacobi_read_face");
   const BlockHost& B = h->plan.blocks[block];
   const int parity = (int)(grid_local_iter(h, B.grid) & 1);
-  const size_t n = (size_t)face_elems_host(B, face) * h->plan.elem;
-  JGB_CUDA(cudaMemcpyAsync(dst, h->ws + B.recv_off[face][parity], n, cudaMemcpyDeviceToHost, S(stream)));
+  // The slot rows are padded (x-faces to ry, the others to rx): copy the
+  // face's own entries, row by row, into the compact layout.
+  const size_t e = h->plan.elem;
+  const int64_t width = face < 2 ? B.extent[1] : B.extent[0];
+  const int64_t pitch = face < 2 ? B.ry : B.rx;
+  const int64_t height = face < 4 ? B.extent[2] : B.extent[1];
+  JGB_CUDA(cudaMemcpy2DAsync(dst, width * e, h->ws + B.recv_off[face][parity], pitch * e, width * e, height,
+                             cudaMemcpyDeviceToHost, S(stream)));
   JGB_CUDA(cudaStreamSynchronize(S(stream)));
   return JACOBI_OK;
 }

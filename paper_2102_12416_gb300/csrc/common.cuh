@@ -20,13 +20,18 @@ enum DevError : uint32_t {
 };
 
 // One block of the decomposition (a "chare" of the paper's Jacobi3D).
-// Interior storage: plane k starts at k * plane_pitch elements, row j of a
-// plane at j * nx; plane_pitch >= nx*ny is rounded up so every plane starts on
-// a 16-byte boundary.  Receive slots, by face, laid out
-//   xm/xp: [k][j] (nz x ny)   ym/yp: [k][i] (nz x nx)   zm/zp: [j][i] (ny x nx)
-// recv[f][p] is read at iterations with parity p; for a Dirichlet face both
-// parities point at the same constant boundary buffer.  send[f][p] is the
-// neighbour's recv[opposite(f)][p] (written with the NEW iterate, at parity
+// Interior storage is padded: a row holds rx >= nx elements (nx rounded up to
+// a 16-byte vector) and a plane ry >= ny rows (ny rounded up to 4), so every
+// row starts on a 16-byte boundary and the plane-streaming kernels take any
+// block shape.  Plane k starts at k * plane_pitch (>= rx * ry, rounded up) and
+// point (i, j, k) sits at k * plane_pitch + j * rx + i.  Receive slots, by
+// face, use the same padded pitches:
+//   xm/xp: [k][j] (nz x ry)   ym/yp: [k][i] (nz x rx)   zm/zp: [j][i] (ry x rx)
+// Padding entries never feed a real point: the kernels substitute the ghost
+// value for any padding lane or row a real point would read.  recv[f][p] is
+// read at iterations with parity p; for a Dirichlet face both parities point
+// at the same constant boundary buffer.  send[f][p] is the neighbour's
+// recv[opposite(f)][p] (written with the NEW iterate, at parity
 // p = (it + 1) & 1), or null on a Dirichlet face.
 struct BlockDev {
   void* u[2];
@@ -36,14 +41,15 @@ struct BlockDev {
   int32_t grid;
   int64_t plane_pitch;
   int32_t nbr[6];
-  int32_t pad_[2];
+  int32_t rx, ry;
 };
 
 // One CTA's share of a step over the z-range [z0, z1) of block `block`:
 //   x0 >= 0: the TX x TY tile of columns at (x0, y0);
-//   x0 <  0: rows [ya, yb) of the x-y planes, streamed through shared
-//            memory, each thread computing y0 rows (1, 2 or 4) of one
-//            16-byte vector column.
+//   x0 <  0: padded rows [ya, yb) of the x-y planes, streamed through
+//            shared memory by a CTA of (y0 & 15) consumer warps (2, 4 or 8;
+//            y0 & 16 marks a block with padding), each
+//            thread computing 4 rows of one 16-byte vector column.
 // `slot` indexes the reduction partials.
 struct WorkItem {
   int32_t block;

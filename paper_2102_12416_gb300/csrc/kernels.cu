@@ -35,33 +35,42 @@ template <typename T> __device__ __forceinline__ T to_state(double v);
 template <> __device__ __forceinline__ double to_state<double>(double v) { return v; }
 template <> __device__ __forceinline__ float to_state<float>(double v) { return __double2float_rn(v); }
 
-// Global padded coordinates of element e of face f of block (B, G).
-__device__ __forceinline__ void face_coords(const BlockDev& B, const BlockGeom& G, int f, int64_t e,
+// Entries of the (padded) receive slot of face f.
+__device__ __forceinline__ int64_t face_elems(const BlockDev& B, int f) {
+  if (f == XM || f == XP) return (int64_t)B.nz * B.ry;
+  if (f == YM || f == YP) return (int64_t)B.nz * B.rx;
+  return (int64_t)B.ry * B.rx;
+}
+
+// Global padded grid coordinates of slot entry e of face f of block (B, G);
+// false for a padding entry.
+__device__ __forceinline__ bool face_coords(const BlockDev& B, const BlockGeom& G, int f, int64_t e,
                                             int64_t& gi, int64_t& gj, int64_t& gk) {
   const int nx = B.nx, ny = B.ny, nz = B.nz;
   if (f == XM || f == XP) {
-    const int64_t k = e / ny, j = e % ny;
+    const int64_t k = e / B.ry, j = e % B.ry;
     gi = G.ox + (f == XM ? 0 : nx + 1);
     gj = G.oy + 1 + j;
     gk = G.oz + 1 + k;
-  } else if (f == YM || f == YP) {
-    const int64_t k = e / nx, i = e % nx;
+    return j < ny;
+  }
+  if (f == YM || f == YP) {
+    const int64_t k = e / B.rx, i = e % B.rx;
     gi = G.ox + 1 + i;
     gj = G.oy + (f == YM ? 0 : ny + 1);
     gk = G.oz + 1 + k;
-  } else {
-    const int64_t j = e / nx, i = e % nx;
-    gi = G.ox + 1 + i;
-    gj = G.oy + 1 + j;
-    gk = G.oz + (f == ZM ? 0 : nz + 1);
+    return i < nx;
   }
-  (void)nz;
+  const int64_t j = e / B.rx, i = e % B.rx;
+  gi = G.ox + 1 + i;
+  gj = G.oy + 1 + j;
+  gk = G.oz + (f == ZM ? 0 : nz + 1);
+  return i < nx && j < ny;
 }
 
-__device__ __forceinline__ int64_t face_elems(const BlockDev& B, int f) {
-  if (f == XM || f == XP) return (int64_t)B.nz * B.ny;
-  if (f == YM || f == YP) return (int64_t)B.nz * B.nx;
-  return (int64_t)B.ny * B.nx;
+// Offset of interior point (i, j, k) in the block's padded storage.
+__device__ __forceinline__ int64_t cell(const BlockDev& B, int64_t i, int64_t j, int64_t k) {
+  return k * B.plane_pitch + j * B.rx + i;
 }
 
 template <typename T>
@@ -74,7 +83,7 @@ __global__ void k_init_interior(const BlockDev* __restrict__ blocks, const Block
   const int64_t nx = B.nx, ny = B.ny, n = nx * ny * B.nz;
   for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
     const int64_t i = e % nx, j = (e / nx) % ny, k = e / (nx * ny);
-    U[k * B.plane_pitch + j * nx + i] = to_state<T>(init_value(I, G.ox + 1 + i, G.oy + 1 + j, G.oz + 1 + k));
+    U[cell(B, i, j, k)] = to_state<T>(init_value(I, G.ox + 1 + i, G.oy + 1 + j, G.oz + 1 + k));
   }
 }
 
@@ -89,8 +98,7 @@ __global__ void k_init_slots(const BlockDev* __restrict__ blocks, const BlockGeo
   const int64_t n = face_elems(B, f);
   for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
     int64_t gi, gj, gk;
-    face_coords(B, G, f, e, gi, gj, gk);
-    S[e] = to_state<T>(init_value(I, gi, gj, gk));
+    if (face_coords(B, G, f, e, gi, gj, gk)) S[e] = to_state<T>(init_value(I, gi, gj, gk));
   }
 }
 
@@ -106,7 +114,7 @@ __global__ void k_scatter(const BlockDev* __restrict__ blocks, const BlockGeom* 
     const int64_t nx = B.nx, ny = B.ny, n = nx * ny * B.nz;
     for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
       const int64_t i = e % nx, j = (e / nx) % ny, k = e / (nx * ny);
-      U[k * B.plane_pitch + j * nx + i] = src[((G.oz + 1 + k) * py + (G.oy + 1 + j)) * px + (G.ox + 1 + i)];
+      U[cell(B, i, j, k)] = src[((G.oz + 1 + k) * py + (G.oy + 1 + j)) * px + (G.ox + 1 + i)];
     }
   } else {
     const int f = blockIdx.y - 1;
@@ -114,8 +122,7 @@ __global__ void k_scatter(const BlockDev* __restrict__ blocks, const BlockGeom* 
     const int64_t n = face_elems(B, f);
     for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
       int64_t gi, gj, gk;
-      face_coords(B, G, f, e, gi, gj, gk);
-      S[e] = src[(gk * py + gj) * px + gi];
+      if (face_coords(B, G, f, e, gi, gj, gk)) S[e] = src[(gk * py + gj) * px + gi];
     }
   }
 }
@@ -134,7 +141,7 @@ __global__ void k_gather(const BlockDev* __restrict__ blocks, const BlockGeom* _
     for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
       const int64_t i = e % nx, j = (e / nx) % ny, k = e / (nx * ny);
       dst[((G.oz + off + k) * py + (G.oy + off + j)) * px + (G.ox + off + i)] =
-          U[k * B.plane_pitch + j * nx + i];
+          U[cell(B, i, j, k)];
     }
   } else if (padded) {
     const int f = blockIdx.y - 1;
@@ -143,8 +150,7 @@ __global__ void k_gather(const BlockDev* __restrict__ blocks, const BlockGeom* _
     const int64_t n = face_elems(B, f);
     for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
       int64_t gi, gj, gk;
-      face_coords(B, G, f, e, gi, gj, gk);
-      dst[(gk * py + gj) * px + gi] = S[e];
+      if (face_coords(B, G, f, e, gi, gj, gk)) dst[(gk * py + gj) * px + gi] = S[e];
     }
   }
 }
@@ -157,7 +163,7 @@ __global__ void __launch_bounds__(kThreads) k_bnorm(StepLaunch a) {
   const WorkItem w = a.items[blockIdx.x];
   const BlockDev& B = a.blocks[w.block];
   const int p = (int)((a.it - a.grids[B.grid].start_iter) & 1);
-  const int nx = B.nx, ny = B.ny, nz = B.nz;
+  const int nx = B.nx, ny = B.ny, nz = B.nz, rx = B.rx, ry = B.ry;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int xa = w.x0 >= 0 ? w.x0 : 0, ya = w.x0 >= 0 ? w.y0 : 0;
   const int xb = w.x0 >= 0 ? w.x0 + TX : nx, yb = w.x0 >= 0 ? w.y0 + TY : ny;
@@ -168,12 +174,12 @@ __global__ void __launch_bounds__(kThreads) k_bnorm(StepLaunch a) {
       if (i >= nx || j >= ny) continue;
       for (int k = w.z0; k < w.z1; ++k) {
         double v[6] = {0, 0, 0, 0, 0, 0};
-        if (i == 0 && B.nbr[XM] < 0) v[0] = (double)((const T*)B.recv[XM][p])[(int64_t)k * ny + j];
-        if (i == nx - 1 && B.nbr[XP] < 0) v[1] = (double)((const T*)B.recv[XP][p])[(int64_t)k * ny + j];
-        if (j == 0 && B.nbr[YM] < 0) v[2] = (double)((const T*)B.recv[YM][p])[(int64_t)k * nx + i];
-        if (j == ny - 1 && B.nbr[YP] < 0) v[3] = (double)((const T*)B.recv[YP][p])[(int64_t)k * nx + i];
-        if (k == 0 && B.nbr[ZM] < 0) v[4] = (double)((const T*)B.recv[ZM][p])[(int64_t)j * nx + i];
-        if (k == nz - 1 && B.nbr[ZP] < 0) v[5] = (double)((const T*)B.recv[ZP][p])[(int64_t)j * nx + i];
+        if (i == 0 && B.nbr[XM] < 0) v[0] = (double)((const T*)B.recv[XM][p])[(int64_t)k * ry + j];
+        if (i == nx - 1 && B.nbr[XP] < 0) v[1] = (double)((const T*)B.recv[XP][p])[(int64_t)k * ry + j];
+        if (j == 0 && B.nbr[YM] < 0) v[2] = (double)((const T*)B.recv[YM][p])[(int64_t)k * rx + i];
+        if (j == ny - 1 && B.nbr[YP] < 0) v[3] = (double)((const T*)B.recv[YP][p])[(int64_t)k * rx + i];
+        if (k == 0 && B.nbr[ZM] < 0) v[4] = (double)((const T*)B.recv[ZM][p])[(int64_t)j * rx + i];
+        if (k == nz - 1 && B.nbr[ZP] < 0) v[5] = (double)((const T*)B.recv[ZP][p])[(int64_t)j * rx + i];
         const double sb =
             __dadd_rn(__dadd_rn(__dadd_rn(v[0], v[1]), __dadd_rn(v[2], v[3])), __dadd_rn(v[4], v[5]));
         acc = fma(sb, sb, acc);
@@ -194,9 +200,9 @@ __global__ void k_emu_check(const BlockDev* __restrict__ blocks, const GridDev* 
   const int p = (int)((it - grids[B.grid].start_iter) & 1);
   const uint32_t* U = (const uint32_t*)B.u[p];
   bool bad = false;
-  const int64_t n = (int64_t)B.nx * B.ny;
-  for (int64_t k = 0; k < B.nz && !bad; ++k)
-    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) bad |= U[2 * (k * B.plane_pitch + e) + 1] >= kEmuHiLimit;
+  const int64_t nx = B.nx, ny = B.ny, n = nx * ny * B.nz;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x)
+    bad |= U[2 * cell(B, e % nx, (e / nx) % ny, e / (nx * ny)) + 1] >= kEmuHiLimit;
   for (int f = 0; f < 6; ++f) {
     const uint32_t* S = (const uint32_t*)B.recv[f][p];
     const int64_t m = face_elems(B, f);
@@ -268,14 +274,14 @@ __global__ void k_pack_faces(const BlockDev* __restrict__ blocks, void* const* s
   const int p = (int)((it - grids[B.grid].start_iter) & 1);
   const T* U = (const T*)B.u[p ^ 1];
   T* S = (T*)staging[b * 6 + f];
-  const int64_t nx = B.nx, ny = B.ny, nz = B.nz, pp = B.plane_pitch;
+  const int64_t nx = B.nx, ny = B.ny, nz = B.nz, rx = B.rx, ry = B.ry;
   const int64_t n = face_elems(B, f);
-  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {  // padding entries copy padding
     int64_t i, j, k;
-    if (f == XM || f == XP) { k = e / ny; j = e % ny; i = (f == XM) ? 0 : nx - 1; }
-    else if (f == YM || f == YP) { k = e / nx; i = e % nx; j = (f == YM) ? 0 : ny - 1; }
-    else { j = e / nx; i = e % nx; k = (f == ZM) ? 0 : nz - 1; }
-    S[e] = U[k * pp + j * nx + i];
+    if (f == XM || f == XP) { k = e / ry; j = e % ry; i = (f == XM) ? 0 : nx - 1; }
+    else if (f == YM || f == YP) { k = e / rx; i = e % rx; j = (f == YM) ? 0 : ny - 1; }
+    else { j = e / rx; i = e % rx; k = (f == ZM) ? 0 : nz - 1; }
+    S[e] = U[cell(B, i, j, k)];
   }
 }
 

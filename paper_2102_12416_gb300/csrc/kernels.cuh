@@ -26,18 +26,18 @@ struct BlockGeom {
 // 227 KB per CTA, minus room for the kernels' static shared memory).
 constexpr int kMaxStepSmem = 227 * 1024 - 1024;  // 1 KB left for static shared memory
 
-// A plane-streaming item encodes its rows per thread RY and its consumer warps
-// CW in y0 = RY + 16 * CW.  Item kinds of a step launch: 0 = tiles; 1, 2, 3 =
-// streaming with RY = 1, 2, 4 and CW = 8; 4 = RY 4, CW 4; 5 = RY 4, CW 2.
-// Each kind runs its own kernel variant.
-constexpr int kItemKinds = 6;
-__host__ __device__ inline int item_rows(const WorkItem& w) { return w.y0 & 15; }
-__host__ __device__ inline int item_warps(const WorkItem& w) { return w.y0 >> 4; }
+// A plane-streaming item encodes its consumer warps (2, 4 or 8) in the low
+// bits of y0 and, in bit 4, whether its block has padding (ragged rows or
+// planes).  Item kinds of a step launch: 0 = tiles; 1, 2, 3 = streaming with
+// 8, 4, 2 consumer warps; 4, 5, 6 = the same for ragged blocks.  Each kind
+// runs its own kernel variant.
+constexpr int kItemKinds = 7;
+constexpr int kItemRagged = 16;
+__host__ __device__ inline bool item_ragged(const WorkItem& w) { return (w.y0 & kItemRagged) != 0; }
 __host__ __device__ inline int item_kind(const WorkItem& w) {
   if (w.x0 >= 0) return 0;
-  const int ry = item_rows(w), cw = item_warps(w);
-  if (cw == 8) return ry == 1 ? 1 : ry == 2 ? 2 : 3;
-  return cw == 4 ? 4 : 5;
+  const int cw = w.y0 & 15;
+  return (cw == 8 ? 1 : cw == 4 ? 2 : 3) + (item_ragged(w) ? 3 : 0);
 }
 
 struct StepLaunch {
@@ -58,9 +58,23 @@ struct StepLaunch {
   int32_t pad_;
 };
 
+// Streams and events that let the item kinds of one step run side by side:
+// the kinds fork from the caller's stream and join it again before anything
+// after the step (the next iteration reads their faces).  Under stream
+// capture the fork becomes parallel branches of the graph.
+struct KindFork {
+  cudaStream_t aux[kItemKinds] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kItemKinds] = {};
+};
+cudaError_t kind_fork_create(KindFork* f);
+void kind_fork_destroy(KindFork* f);
+
 // Step kernels.  mode flags:
 enum StepMode : int { kWrite = 1, kPack = 2, kResid = 4 };
-cudaError_t launch_step(const StepLaunch& a, int mode, cudaStream_t s);
+// One step over a.items (grouped by kind at a.kind_off).  With `fork`, the
+// kinds run concurrently; without it they run one after another on s.
+cudaError_t launch_step(const StepLaunch& a, int mode, cudaStream_t s, const KindFork* fork = nullptr);
 
 // Explicit exchange: pack every internal face of the NEW iterate into its
 // staging buffer, then copy staging buffers into the neighbours' slots.

@@ -32,6 +32,7 @@ struct BlockHost {
   int64_t origin[3], extent[3];
   int64_t nbr[6];
   int64_t item_begin, item_end;  // items of this block in the full list
+  int64_t rx, ry;                // padded row pitch and rows per plane
   int64_t pitch;                 // elements per z-plane
   size_t u_off[2];
   size_t recv_off[6][2];
@@ -121,6 +122,7 @@ struct jacobi_s {
   jgb::GridNorm* h_norms = nullptr;  // pinned, read back from d_norms
   uint32_t* h_err = nullptr;        // pinned
 
+  jgb::KindFork fork;             // side-by-side launch of the step's item kinds
   // CUDA graph of the fused path
   cudaGraphExec_t graph = nullptr;
   int64_t graph_iters = 0;

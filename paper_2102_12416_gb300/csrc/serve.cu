@@ -112,6 +112,7 @@ struct serve_s {
   serve_config cfg{};
   int device = 0;
   cudaStream_t stream = nullptr;
+  KindFork fork;  // side-by-side launch of a step's item kinds
   // device tables
   char* dmem = nullptr;
   BlockDev* d_blocks = nullptr;
@@ -219,6 +220,7 @@ int admit(serve_s* s, int si, const Req& q) {
   ENG_CUDA(cudaMemcpyAsync(s->d_inits + si, &ini, sizeof ini, cudaMemcpyHostToDevice, st));
   ENG_CUDA(cudaMemcpyAsync(s->d_slotdev + si, &sd, sizeof sd, cudaMemcpyHostToDevice, st));
   ENG_CUDA(cudaMemcpyAsync(s->d_rec + si, &rec, sizeof rec, cudaMemcpyHostToDevice, st));
+  ENG_CUDA(cudaMemsetAsync(sl.ws, 0, P.bytes, st));  // padding starts at zero
   ENG_CUDA(launch_init(s->d_blocks + sl.block_base, s->d_geom + sl.block_base, (int32_t)nb, s->d_inits,
                        s->cfg.dtype, st));
   StepLaunch a{};
@@ -294,7 +296,7 @@ int run_round(serve_s* s) {
   const int n = (int)s->running.size();
   for (int c = 0; c < s->cfg.round_checks; ++c) {
     a.it = s->it;
-    ENG_CUDA(launch_step(a, kWrite | kPack | kResid, s->stream));
+    ENG_CUDA(launch_step(a, kWrite | kPack | kResid, s->stream, &s->fork));
     ENG_CUDA(launch_reduce(s->d_grids, s->d_norms, s->d_gids, n, s->d_partials, 0, s->stream));
     k_decide<<<(n + 127) / 128, 128, 0, s->stream>>>(s->d_grids, s->d_norms, s->d_slotdev, s->d_rec, s->d_gids, n,
                                                        s->it);
@@ -302,7 +304,7 @@ int run_round(serve_s* s) {
     s->it += 1;
     for (int t = 1; t < s->cfg.check_every; ++t) {
       a.it = s->it;
-      ENG_CUDA(launch_step(a, kWrite | kPack, s->stream));
+      ENG_CUDA(launch_step(a, kWrite | kPack, s->stream, &s->fork));
       s->it += 1;
     }
   }
@@ -441,11 +443,14 @@ int serve_create(const serve_config* cfg, serve_t** out) {
   const size_t o_err = take(64);
   cudaError_t e = cudaGetDevice(&s->device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = kind_fork_create(&s->fork);
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->dmem, off);
   if (e == cudaSuccess) e = cudaMemset(s->dmem, 0, off);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s->h_rec, ns * sizeof(Record));
   if (e != cudaSuccess) {
     if (s->dmem) cudaFree(s->dmem);
+    if (s->h_rec) cudaFreeHost(s->h_rec);
+    kind_fork_destroy(&s->fork);
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return set_error(JACOBI_ENOMEM, "serve_create: %s", cudaGetErrorString(e));
@@ -469,6 +474,7 @@ int serve_create(const serve_config* cfg, serve_t** out) {
   if (e != cudaSuccess) {
     cudaFree(s->dmem);
     cudaFreeHost(s->h_rec);
+    kind_fork_destroy(&s->fork);
     cudaStreamDestroy(s->stream);
     delete s;
     return set_error(JACOBI_ECUDA, "serve_create: %s", cudaGetErrorString(e));
@@ -531,6 +537,7 @@ int serve_destroy(serve_t* s) {
   cudaStreamSynchronize(s->stream);
   cudaFree(s->dmem);
   cudaFreeHost(s->h_rec);
+  kind_fork_destroy(&s->fork);
   cudaStreamDestroy(s->stream);
   delete s;
   return JACOBI_OK;

@@ -115,7 +115,7 @@ template <typename T, int MODE>
 __device__ __forceinline__ double tile_sweep(const BlockDev& B, int p, int x0, int y0, int z0, int z1, int tx,
                                              int ty) {
   const int i = x0 + tx, j = y0 + ty;
-  const int nx = B.nx, ny = B.ny, nz = B.nz;
+  const int nx = B.nx, ny = B.ny, nz = B.nz, rx = B.rx, ry = B.ry;
   double acc = 0.0;
   if (i >= nx || j >= ny) return acc;
   const T* __restrict__ U = (const T*)B.u[p];
@@ -126,7 +126,7 @@ __device__ __forceinline__ double tile_sweep(const BlockDev& B, int p, int x0, i
   const T* rym = (const T*)B.recv[YM][p];
   const T* ryp = (const T*)B.recv[YP][p];
   const T* rzp = (const T*)B.recv[ZP][p];
-  const int64_t col = (int64_t)j * nx + i;
+  const int64_t col = (int64_t)j * rx + i;
   T below = (z0 == 0) ? __ldcg((const T*)B.recv[ZM][p] + col) : U[(int64_t)(z0 - 1) * pp + col];
   T cur = U[(int64_t)z0 * pp + col];
   T* sxm = nullptr; T* sxp = nullptr; T* sym = nullptr; T* syp = nullptr; T* szm = nullptr; T* szp = nullptr;
@@ -141,19 +141,19 @@ __device__ __forceinline__ double tile_sweep(const BlockDev& B, int p, int x0, i
   for (int k = z0; k < z1; ++k) {
     const int64_t o = (int64_t)k * pp + col;
     const T above = (k + 1 < nz) ? U[o + pp] : __ldcg(rzp + col);
-    const T xm = (i > 0) ? U[o - 1] : __ldcg(rxm + (int64_t)k * ny + j);
-    const T xp = (i < nx - 1) ? U[o + 1] : __ldcg(rxp + (int64_t)k * ny + j);
-    const T ym = (j > 0) ? U[o - nx] : __ldcg(rym + (int64_t)k * nx + i);
-    const T yp = (j < ny - 1) ? U[o + nx] : __ldcg(ryp + (int64_t)k * nx + i);
+    const T xm = (i > 0) ? U[o - 1] : __ldcg(rxm + (int64_t)k * ry + j);
+    const T xp = (i < nx - 1) ? U[o + 1] : __ldcg(rxp + (int64_t)k * ry + j);
+    const T ym = (j > 0) ? U[o - rx] : __ldcg(rym + (int64_t)k * rx + i);
+    const T yp = (j < ny - 1) ? U[o + rx] : __ldcg(ryp + (int64_t)k * rx + i);
     const T s = radd(radd(radd(xm, xp), radd(ym, yp)), radd(below, above));
     if (MODE & kWrite) {
       const T v = rmul(s, C6<T>::v);
       V[o] = v;
       if (MODE & kPack) {
-        if (sxm) sxm[(int64_t)k * ny + j] = v;
-        if (sxp) sxp[(int64_t)k * ny + j] = v;
-        if (sym) sym[(int64_t)k * nx + i] = v;
-        if (syp) syp[(int64_t)k * nx + i] = v;
+        if (sxm) sxm[(int64_t)k * ry + j] = v;
+        if (sxp) sxp[(int64_t)k * ry + j] = v;
+        if (sym) sym[(int64_t)k * rx + i] = v;
+        if (syp) syp[(int64_t)k * rx + i] = v;
         if (k == 0 && szm) szm[col] = v;
         if (k == nz - 1 && szp) szp[col] = v;
       }
@@ -189,10 +189,12 @@ __device__ __forceinline__ T nsum(T xm, T xp, T ym, T yp, T zm, T zp) {
   return radd(radd(radd(xm, xp), radd(ym, yp)), radd(zm, zp));
 }
 
-// Shared-memory stage of one plane of a row window [ya, yb) of block B: rows
-// ra..rb-1 of the plane (the window plus one neighbour row on each side that
-// exists), then the x ghosts of the window's rows (xm, xp), then the y ghost
-// rows (ym, yp; filled only at the block's edges, where they are needed).
+// Shared-memory stage of one plane of a padded row window [ya, yb) of block
+// B: rows ra..rb-1 of the plane (the window plus one neighbour row on each
+// side that exists), then the x ghosts of the window's rows (xm, xp), then the
+// y ghost rows (ym, yp; filled only at the block's edges, where they are
+// needed).  Rows have the padded pitch rx; windows start on multiples of 4
+// rows, so every copy is a whole number of 16-byte vectors.
 struct StageLayout {
   int ra, rb;
   uint32_t rows_bytes, xg, yg, bytes;
@@ -202,10 +204,10 @@ template <typename T>
 __device__ __forceinline__ StageLayout stage_layout(const BlockDev& B, int ya, int yb) {
   StageLayout L;
   L.ra = ya > 0 ? ya - 1 : 0;
-  L.rb = yb < B.ny ? yb + 1 : B.ny;
-  L.rows_bytes = (uint32_t)((L.rb - L.ra) * B.nx * sizeof(T));
+  L.rb = yb < B.ry ? yb + 1 : B.ry;
+  L.rows_bytes = (uint32_t)((L.rb - L.ra) * B.rx * sizeof(T));
   L.xg = (uint32_t)((yb - ya) * sizeof(T));
-  L.yg = (uint32_t)(B.nx * sizeof(T));
+  L.yg = (uint32_t)(B.rx * sizeof(T));
   L.o_xm = L.rows_bytes;
   L.o_xp = L.o_xm + L.xg;
   L.o_ym = L.o_xp + L.xg;
@@ -219,20 +221,20 @@ __device__ __forceinline__ StageLayout stage_layout(const BlockDev& B, int ya, i
 template <typename T>
 __device__ __forceinline__ void issue_plane(const BlockDev& B, int p, int z0, int nplanes, int q, int ya, int yb,
                                             const StageLayout& L, unsigned char* dst, uint64_t* bar) {
-  const int nx = B.nx, ny = B.ny, nz = B.nz;
+  const int rx = B.rx, ry = B.ry, nz = B.nz;
   const int kk = z0 - 1 + q;
   const T* src = kk < 0 ? (const T*)B.recv[ZM][p]
                         : (kk >= nz ? (const T*)B.recv[ZP][p] : (const T*)B.u[p] + (int64_t)kk * B.plane_pitch);
   const bool ghosts = q >= 1 && q <= nplanes - 2;
-  const bool gym = ghosts && ya == 0, gyp = ghosts && yb == ny;
+  const bool gym = ghosts && ya == 0, gyp = ghosts && yb == ry;
   mbar_expect_tx(bar, L.rows_bytes + (ghosts ? 2 * L.xg : 0) + (gym ? L.yg : 0) + (gyp ? L.yg : 0));
-  bulk_g2s(dst, src + (int64_t)L.ra * nx, L.rows_bytes, bar);
+  bulk_g2s(dst, src + (int64_t)L.ra * rx, L.rows_bytes, bar);
   if (ghosts) {
-    bulk_g2s(dst + L.o_xm, (const T*)B.recv[XM][p] + (int64_t)kk * ny + ya, L.xg, bar);
-    bulk_g2s(dst + L.o_xp, (const T*)B.recv[XP][p] + (int64_t)kk * ny + ya, L.xg, bar);
+    bulk_g2s(dst + L.o_xm, (const T*)B.recv[XM][p] + (int64_t)kk * ry + ya, L.xg, bar);
+    bulk_g2s(dst + L.o_xp, (const T*)B.recv[XP][p] + (int64_t)kk * ry + ya, L.xg, bar);
   }
-  if (gym) bulk_g2s(dst + L.o_ym, (const T*)B.recv[YM][p] + (int64_t)kk * nx, L.yg, bar);
-  if (gyp) bulk_g2s(dst + L.o_yp, (const T*)B.recv[YP][p] + (int64_t)kk * nx, L.yg, bar);
+  if (gym) bulk_g2s(dst + L.o_ym, (const T*)B.recv[YM][p] + (int64_t)kk * rx, L.yg, bar);
+  if (gyp) bulk_g2s(dst + L.o_yp, (const T*)B.recv[YP][p] + (int64_t)kk * rx, L.yg, bar);
 }
 
 // What a consumer thread needs from its block, read once per work item into
@@ -241,6 +243,7 @@ __device__ __forceinline__ void issue_plane(const BlockDev& B, int p, int z0, in
 template <typename T>
 struct PlaneView {
   int nx, ny, nz, pn;      // extents; parity of the new iterate
+  int rx, ry;              // padded row pitch and rows per plane
   int64_t pitch;
   T* V;                    // new iterate
   const BlockDev* B;       // for the send pointers, read by edge threads only
@@ -252,6 +255,8 @@ __device__ __forceinline__ PlaneView<T> plane_view(const BlockDev& B, int p) {
   v.ny = B.ny;
   v.nz = B.nz;
   v.pn = p ^ 1;
+  v.rx = B.rx;
+  v.ry = B.ry;
   v.pitch = B.plane_pitch;
   v.V = (T*)B.u[p ^ 1];
   v.B = &B;
@@ -263,41 +268,57 @@ __device__ __forceinline__ T* send_slot(const PlaneView<T>& O, int f) {
   return (T*)__ldg((const unsigned long long*)&O.B->send[f][O.pn]);
 }
 
-// Compute plane k of rows [j0, j0 + RY) (inside the window [ya, yb)) from the
-// stages holding planes k - 1, k, k + 1.  tx = vector column.
-template <typename T, int RY, int MODE, bool EMU>
+// Compute plane k of padded rows [j0, j0 + RY) (inside the window [ya, yb))
+// from the stages holding planes k - 1, k, k + 1.  tx = vector column.  With
+// RAG (a block whose nx is not a whole number of vectors or whose ny is not a
+// multiple of 4), rows at or past ny and lanes at or past nx are padding:
+// their values are replaced by the y (x) ghost before use, so the last real
+// row (column) sees its ghost, and they are neither summed into the residual
+// nor stored.  Without RAG there is no padding and none of those checks.
+template <typename T, int RY, int MODE, bool EMU, bool RAG>
 __device__ __forceinline__ double stream_plane(const PlaneView<T>& O, int k, int ya, const StageLayout& L,
                                                const unsigned char* sm, const unsigned char* sc,
                                                const unsigned char* sp, int tx, int j0) {
   constexpr int VEC = V16<T>::N;
   const int nx = O.nx, ny = O.ny, nz = O.nz;
+  const int rx = RAG ? O.rx : nx, ry = RAG ? O.ry : ny;  // equal without padding
   const int i0 = tx * VEC;
-  const T* Pm = (const T*)sm - L.ra * nx;  // row j of a plane at P + j * nx
-  const T* Pc = (const T*)sc - L.ra * nx;
-  const T* Pp = (const T*)sp - L.ra * nx;
+  const T* Pm = (const T*)sm - L.ra * rx;  // row j of a plane at P + j * rx
+  const T* Pc = (const T*)sc - L.ra * rx;
+  const T* Pp = (const T*)sp - L.ra * rx;
   const T* Gxm = (const T*)(sc + L.o_xm) - ya;  // x ghost of row j at G[j]
   const T* Gxp = (const T*)(sc + L.o_xp) - ya;
   const T* Gym = (const T*)(sc + L.o_ym);
   const T* Gyp = (const T*)(sc + L.o_yp);
   T* __restrict__ V = O.V + (int64_t)k * O.pitch;
+  const int ql = nx - 1 - i0;  // last real lane of this vector column (< VEC - 1: ragged)
 
   T c[RY][VEC];
 #pragma unroll
-  for (int r = 0; r < RY; ++r) V16<T>::load(Pc + (j0 + r) * nx + i0, c[r]);
+  for (int r = 0; r < RY; ++r) V16<T>::load(!RAG || j0 + r < ny ? Pc + (j0 + r) * rx + i0 : Gyp + i0, c[r]);
+  if (RAG && ql < VEC - 1) {
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      const T g = Gxp[j0 + r];
+#pragma unroll
+      for (int q = 1; q < VEC; ++q)
+        if (q > ql) c[r][q] = g;
+    }
+  }
   T top[VEC], bot[VEC];
-  V16<T>::load(j0 > 0 ? Pc + (j0 - 1) * nx + i0 : Gym + i0, top);
-  V16<T>::load(j0 + RY < ny ? Pc + (j0 + RY) * nx + i0 : Gyp + i0, bot);
+  V16<T>::load(j0 > 0 ? Pc + (j0 - 1) * rx + i0 : Gym + i0, top);
+  V16<T>::load(j0 + RY < ny ? Pc + (j0 + RY) * rx + i0 : Gyp + i0, bot);
   double acc = 0.0;
 #pragma unroll
   for (int r = 0; r < RY; ++r) {
     const int j = j0 + r;
     T zm[VEC], zp[VEC];
-    V16<T>::load(Pm + j * nx + i0, zm);
-    V16<T>::load(Pp + j * nx + i0, zp);
+    V16<T>::load(Pm + j * rx + i0, zm);
+    V16<T>::load(Pp + j * rx + i0, zp);
     const T* ym = r == 0 ? top : c[r > 0 ? r - 1 : 0];
     const T* yp = r == RY - 1 ? bot : c[r < RY - 1 ? r + 1 : 0];
-    const T left = i0 > 0 ? Pc[j * nx + i0 - 1] : Gxm[j];
-    const T right = i0 + VEC < nx ? Pc[j * nx + i0 + VEC] : Gxp[j];
+    const T left = i0 > 0 ? Pc[j * rx + i0 - 1] : Gxm[j];
+    const T right = i0 + VEC < nx ? Pc[j * rx + i0 + VEC] : Gxp[j];
     T v[VEC];
 #pragma unroll
     for (int q = 0; q < VEC; ++q) {
@@ -305,34 +326,43 @@ __device__ __forceinline__ double stream_plane(const PlaneView<T>& O, int k, int
       const T xp = q == VEC - 1 ? right : c[r][q < VEC - 1 ? q + 1 : 0];
       const T s = nsum<T, EMU>(xm, xp, ym[q], yp[q], zm[q], zp[q]);
       v[q] = rmul(s, C6<T>::v);
-      if (MODE & kResid) acc += resid2<T>(xm, xp, ym[q], yp[q], zm[q], zp[q], s, c[r][q]);
+      if (MODE & kResid) {
+        const double e2 = resid2<T>(xm, xp, ym[q], yp[q], zm[q], zp[q], s, c[r][q]);
+        acc += (!RAG || (q <= ql && j < ny)) ? e2 : 0.0;
+      }
     }
-    if (MODE & kWrite) {
-      V16<T>::store(V + j * nx + i0, v);
+    if ((MODE & kWrite) && (!RAG || j < ny)) {
+      V16<T>::store(V + j * rx + i0, v);
       if (MODE & kPack) {
         if (i0 == 0) {
           T* d = send_slot(O, XM);
-          if (d) d[(int64_t)k * ny + j] = v[0];
+          if (d) d[(int64_t)k * ry + j] = v[0];
         }
-        if (i0 + VEC == nx) {
+        if (ql < VEC) {
           T* d = send_slot(O, XP);
-          if (d) d[(int64_t)k * ny + j] = v[VEC - 1];
+          T last = v[VEC - 1];
+          if (RAG) {
+#pragma unroll
+            for (int q = 0; q < VEC - 1; ++q)
+              if (q == ql) last = v[q];
+          }
+          if (d) d[(int64_t)k * ry + j] = last;
         }
         if (j == 0) {
           T* d = send_slot(O, YM);
-          if (d) V16<T>::store(d + (int64_t)k * nx + i0, v);
+          if (d) V16<T>::store(d + (int64_t)k * rx + i0, v);
         }
         if (j == ny - 1) {
           T* d = send_slot(O, YP);
-          if (d) V16<T>::store(d + (int64_t)k * nx + i0, v);
+          if (d) V16<T>::store(d + (int64_t)k * rx + i0, v);
         }
         if (k == 0) {
           T* d = send_slot(O, ZM);
-          if (d) V16<T>::store(d + j * nx + i0, v);
+          if (d) V16<T>::store(d + j * rx + i0, v);
         }
         if (k == nz - 1) {
           T* d = send_slot(O, ZP);
-          if (d) V16<T>::store(d + j * nx + i0, v);
+          if (d) V16<T>::store(d + j * rx + i0, v);
         }
       }
     }
@@ -349,9 +379,10 @@ __device__ double stream_item(const BlockDev& B, int p, const WorkItem& w, Ring&
                               uint64_t wait_ns, bool emu, bool& ok) {
   constexpr int VEC = V16<T>::N;
   const int tid = threadIdx.x;
-  const int txv = B.nx / VEC;
+  const int txv = B.rx / VEC;
   const int tx = tid % txv, j0 = w.ya + (tid / txv) * RY;
   const bool active = j0 < w.yb;
+  const bool rag = item_ragged(w);
   const int S = ring.S;
   const StageLayout L = stage_layout<T>(B, w.ya, w.yb);
   const PlaneView<T> O = plane_view<T>(B, p);
@@ -390,10 +421,14 @@ __device__ double stream_item(const BlockDev& B, int p, const WorkItem& w, Ring&
       const unsigned char* sm = ring.stages + (size_t)((q - 1) % S) * L.bytes;
       const unsigned char* sc = ring.stages + (size_t)(q % S) * L.bytes;
       const unsigned char* sp = ring.stages + (size_t)((q + 1) % S) * L.bytes;
-      if (sizeof(T) == 8 && emu)
-        acc += stream_plane<T, RY, MODE, true>(O, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
-      else
-        acc += stream_plane<T, RY, MODE, false>(O, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
+      const int kq = w.z0 - 1 + q;
+      if (rag) {
+        if (sizeof(T) == 8 && emu) acc += stream_plane<T, RY, MODE, true, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+        else acc += stream_plane<T, RY, MODE, false, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+      } else {
+        if (sizeof(T) == 8 && emu) acc += stream_plane<T, RY, MODE, true, false>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+        else acc += stream_plane<T, RY, MODE, false, false>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+      }
     }
   }
   ok = __syncthreads_and(good) != 0;
@@ -418,11 +453,7 @@ __device__ double run_item(const BlockDev& B, int p, const WorkItem& w, Ring& ri
                            uint64_t wait_ns, bool emu, bool& ok) {
   ok = true;
   if (w.x0 >= 0) return tile_sweep<T, MODE>(B, p, w.x0, w.y0, w.z0, w.z1, threadIdx.x % TX, threadIdx.x / TX);
-  switch (item_rows(w)) {
-    case 1: return stream_item<T, 1, MODE>(B, p, w, ring, err, wait_ns, emu, ok);
-    case 2: return stream_item<T, 2, MODE>(B, p, w, ring, err, wait_ns, emu, ok);
-    default: return stream_item<T, 4, MODE>(B, p, w, ring, err, wait_ns, emu, ok);
-  }
+  return stream_item<T, 4, MODE>(B, p, w, ring, err, wait_ns, emu, ok);
 }
 
 __device__ __forceinline__ Ring ring_setup(unsigned char* smem, int S) {
@@ -474,7 +505,7 @@ template <int CW> struct StreamShape {
   static constexpr int min_blocks = 65536 / (threads * 72);
 };
 
-template <typename T, int RY, int CW, int MODE>
+template <typename T, int RY, int CW, bool RAG, int MODE>
 __global__ void __launch_bounds__(StreamShape<CW>::threads, StreamShape<CW>::min_blocks) k_stream(StepLaunch a) {
   constexpr int kConsumerWarps = CW;
   constexpr int kStreamThreads = StreamShape<CW>::threads;
@@ -524,7 +555,7 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, StreamShape<CW>::min
     // ---- consumers ----
     const bool emu = sizeof(T) == 8 && a.emu && a.norms && a.norms[B.grid].emu_bad == 0u;
     const PlaneView<T> O = plane_view<T>(B, p);
-    const int txv = O.nx / VEC;
+    const int txv = O.rx / VEC;
     const int tx = tid % txv, j0 = w.ya + (tid / txv) * RY;
     const bool active = j0 < w.yb;
     bool good = true;
@@ -541,9 +572,9 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, StreamShape<CW>::min
         const unsigned char* sc = stages + (size_t)(q % S) * L.bytes;
         const unsigned char* sp = stages + (size_t)((q + 1) % S) * L.bytes;
         if (sizeof(T) == 8 && emu)
-          acc += stream_plane<T, RY, MODE, true>(O, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
+          acc += stream_plane<T, RY, MODE, true, RAG>(O, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
         else
-          acc += stream_plane<T, RY, MODE, false>(O, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
+          acc += stream_plane<T, RY, MODE, false, RAG>(O, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(empty + (q - 1) % S);
@@ -625,44 +656,67 @@ cudaError_t set_smem_attr(K kernel, bool& done) {
   return e;
 }
 
-template <typename T, int RY, int CW, int MODE>
+template <typename T, int RY, int CW, bool RAG, int MODE>
 cudaError_t launch_stream(const StepLaunch& a, cudaStream_t s) {
   static bool done = false;
-  cudaError_t e = set_smem_attr(k_stream<T, RY, CW, MODE>, done);
+  cudaError_t e = set_smem_attr(k_stream<T, RY, CW, RAG, MODE>, done);
   if (e != cudaSuccess) return e;
-  k_stream<T, RY, CW, MODE><<<a.n_items, StreamShape<CW>::threads, a.smem, s>>>(a);
+  k_stream<T, RY, CW, RAG, MODE><<<a.n_items, StreamShape<CW>::threads, a.smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T, int MODE>
-cudaError_t launch_kinds(const StepLaunch& a, cudaStream_t s) {
-  for (int kind = 0; kind < kItemKinds; ++kind) {
-    StepLaunch b = a;
-    b.items = a.items + a.kind_off[kind];
-    b.n_items = a.kind_off[kind + 1] - a.kind_off[kind];
-    if (b.n_items <= 0) continue;
-    cudaError_t e = cudaSuccess;
-    switch (kind) {
-      case 0: k_tiles<T, MODE><<<b.n_items, kThreads, 0, s>>>(b); e = cudaGetLastError(); break;
-      case 1: e = launch_stream<T, 1, 8, MODE>(b, s); break;
-      case 2: e = launch_stream<T, 2, 8, MODE>(b, s); break;
-      case 3: e = launch_stream<T, 4, 8, MODE>(b, s); break;
-      case 4: e = launch_stream<T, 4, 4, MODE>(b, s); break;
-      default: e = launch_stream<T, 4, 2, MODE>(b, s); break;
-    }
-    if (e != cudaSuccess) return e;
+cudaError_t launch_kind(const StepLaunch& a, int kind, cudaStream_t s) {
+  StepLaunch b = a;
+  b.items = a.items + a.kind_off[kind];
+  b.n_items = a.kind_off[kind + 1] - a.kind_off[kind];
+  switch (kind) {
+    case 0: k_tiles<T, MODE><<<b.n_items, kThreads, 0, s>>>(b); return cudaGetLastError();
+    case 1: return launch_stream<T, 4, 8, false, MODE>(b, s);
+    case 2: return launch_stream<T, 4, 4, false, MODE>(b, s);
+    case 3: return launch_stream<T, 4, 2, false, MODE>(b, s);
+    case 4: return launch_stream<T, 4, 8, true, MODE>(b, s);
+    case 5: return launch_stream<T, 4, 4, true, MODE>(b, s);
+    default: return launch_stream<T, 4, 2, true, MODE>(b, s);
   }
-  return cudaSuccess;
+}
+
+template <typename T, int MODE>
+cudaError_t launch_kinds(const StepLaunch& a, cudaStream_t s, const KindFork* fork) {
+  // Non-empty kinds, largest first (it is launched first and fills the GPU;
+  // the smaller ones fill in around it).
+  int order[kItemKinds], nk = 0;
+  for (int kind = 0; kind < kItemKinds; ++kind)
+    if (a.kind_off[kind + 1] > a.kind_off[kind]) order[nk++] = kind;
+  auto size = [&](int k) { return a.kind_off[k + 1] - a.kind_off[k]; };
+  for (int i = 1; i < nk; ++i)
+    for (int j = i; j > 0 && size(order[j]) > size(order[j - 1]); --j) std::swap(order[j], order[j - 1]);
+  if (!fork || nk <= 1) {
+    for (int i = 0; i < nk; ++i) {
+      cudaError_t e = launch_kind<T, MODE>(a, order[i], s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaEventRecord(fork->fork, s);
+  for (int i = 1; i < nk && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(fork->aux[i], fork->fork, 0);
+  if (e == cudaSuccess) e = launch_kind<T, MODE>(a, order[0], s);
+  for (int i = 1; i < nk && e == cudaSuccess; ++i) {
+    e = launch_kind<T, MODE>(a, order[i], fork->aux[i]);
+    if (e == cudaSuccess) e = cudaEventRecord(fork->join[i], fork->aux[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fork->join[i], 0);
+  }
+  return e;
 }
 
 template <typename T>
-cudaError_t launch_step_t(const StepLaunch& a, int mode, cudaStream_t s) {
+cudaError_t launch_step_t(const StepLaunch& a, int mode, cudaStream_t s, const KindFork* f) {
   if (a.n_items <= 0) return cudaSuccess;
   switch (mode) {
-    case kWrite | kPack: return launch_kinds<T, kWrite | kPack>(a, s);
-    case kWrite | kPack | kResid: return launch_kinds<T, kWrite | kPack | kResid>(a, s);
-    case kWrite: return launch_kinds<T, kWrite>(a, s);
-    case kResid: return launch_kinds<T, kResid>(a, s);
+    case kWrite | kPack: return launch_kinds<T, kWrite | kPack>(a, s, f);
+    case kWrite | kPack | kResid: return launch_kinds<T, kWrite | kPack | kResid>(a, s, f);
+    case kWrite: return launch_kinds<T, kWrite>(a, s, f);
+    case kResid: return launch_kinds<T, kResid>(a, s, f);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -680,8 +734,29 @@ const void* persist_fn() {
 
 }  // namespace
 
-cudaError_t launch_step(const StepLaunch& a, int mode, cudaStream_t s) {
-  return a.dtype == 0 ? launch_step_t<double>(a, mode, s) : launch_step_t<float>(a, mode, s);
+cudaError_t launch_step(const StepLaunch& a, int mode, cudaStream_t s, const KindFork* fork) {
+  return a.dtype == 0 ? launch_step_t<double>(a, mode, s, fork) : launch_step_t<float>(a, mode, s, fork);
+}
+
+cudaError_t kind_fork_create(KindFork* f) {
+  cudaError_t e = cudaEventCreateWithFlags(&f->fork, cudaEventDisableTiming);
+  for (int k = 0; k < kItemKinds && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&f->aux[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->join[k], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) kind_fork_destroy(f);
+  return e;
+}
+
+void kind_fork_destroy(KindFork* f) {
+  if (f->fork) cudaEventDestroy(f->fork);
+  f->fork = nullptr;
+  for (int k = 0; k < kItemKinds; ++k) {
+    if (f->aux[k]) cudaStreamDestroy(f->aux[k]);
+    if (f->join[k]) cudaEventDestroy(f->join[k]);
+    f->aux[k] = nullptr;
+    f->join[k] = nullptr;
+  }
 }
 
 int persistent_max_ctas(int dtype, int smem) {

@@ -172,6 +172,7 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
     units += cw ? (B.ry + ch - 1) / ch : ((B.extent[0] + TX - 1) / TX) * ((B.extent[1] + TY - 1) / TY);
     maxz = std::max(maxz, B.extent[2]);
   }
+  if (target_items <= 0) target_items = dtype == JACOBI_F64 ? kTargetItemsF64 : kTargetItemsF32;
   int64_t zc = maxz;
   while (zc > 2 && units * ((maxz + zc - 1) / zc) < target_items) zc = (zc + 1) / 2;
   for (GridHost& G : P->grids) {

@@ -67,12 +67,16 @@ struct Plan {
   size_t bytes = 0;
 };
 
-// Default work-item target of a handle: enough CTAs to fill the GPU a few
-// times over.  The server plans each request alone with a target of 1 (whole
-// blocks per item): many requests run at once, so each needs no splitting.
-constexpr int64_t kTargetItems = 2048;
+// Default work-item target of a handle (target_items <= 0): enough CTAs to
+// fill the GPU several times over.  The FP64 kernel is bound by arithmetic, so
+// finer items (better balance across SMs) pay; the FP32 kernel is bound by
+// memory, where each z-chunk re-reads two halo planes, so it takes fewer.
+// The server plans each request alone with a target of 1 (whole blocks per
+// item): many requests run at once, so each needs no splitting.
+constexpr int64_t kTargetItemsF64 = 4096;
+constexpr int64_t kTargetItemsF32 = 2048;
 int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* splits, jacobi_dtype dtype,
-               const jacobi_init* inits, Plan* out, int64_t target_items = kTargetItems);
+               const jacobi_init* inits, Plan* out, int64_t target_items = 0);
 
 // Device block table entries of a plan whose workspace starts at `ws`; block
 // and neighbour ids are offset by `base`; grid_override >= 0 replaces every

@@ -257,7 +257,7 @@ def channel_sweep(jg, torch, s, stream):
     return out
 
 
-SERVE_CFG = dict(tol=1e-6, cap=20000, check_every=100, block=(32, 32, 32), budget=120 << 30, slots=128,
+SERVE_CFG = dict(tol=1e-6, cap=20000, check_every=100, block=(32, 32, 32), budget=120 << 30, slots=256,
                  stall_checks=20, noise_amp=1e-3)
 
 

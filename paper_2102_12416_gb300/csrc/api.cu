@@ -89,7 +89,7 @@ static int64_t face_points_host(const BlockHost& b, int f) {
 }
 
 int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* splits, jacobi_dtype dtype,
-               const jacobi_init* inits, Plan* P, int64_t target_items) {
+               const jacobi_init* inits, Plan* P, int64_t target_items, int64_t min_chunk) {
   if (n_grids < 1 || !grids || !splits) return set_error(JACOBI_EINVAL, "need at least one grid");
   if (dtype != JACOBI_F64 && dtype != JACOBI_F32) return set_error(JACOBI_EINVAL, "bad dtype %d", (int)dtype);
   *P = Plan();
@@ -153,8 +153,8 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
   // Work items.  Blocks that fit the plane-streaming path get one item per
   // z-chunk; the others one item per TX x TY tile and z-chunk.  The chunk is
   // the largest power-of-two fraction of the tallest block that still gives
-  // at least `target_items` items (or 2 planes), so small problems still
-  // spread over many CTAs while large ones stream whole blocks.
+  // at least `target_items` items (or min_chunk planes, at least 2), so small
+  // problems still spread over many CTAs while large ones stream whole blocks.
   std::vector<int> warps(P->blocks.size());
   std::vector<int64_t> chunks(P->blocks.size());
   int64_t units = 0, maxz = 0;
@@ -174,7 +174,8 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
   }
   if (target_items <= 0) target_items = dtype == JACOBI_F64 ? kTargetItemsF64 : kTargetItemsF32;
   int64_t zc = maxz;
-  while (zc > 2 && units * ((maxz + zc - 1) / zc) < target_items) zc = (zc + 1) / 2;
+  const int64_t zmin = std::max<int64_t>(min_chunk, 2);
+  while (zc > zmin && (zc + 1) / 2 >= zmin && units * ((maxz + zc - 1) / zc) < target_items) zc = (zc + 1) / 2;
   for (GridHost& G : P->grids) {
     G.item_begin = (int64_t)P->items.size();
     for (int64_t b = G.block_begin; b < G.block_end; ++b) {

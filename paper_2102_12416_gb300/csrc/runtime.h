@@ -71,12 +71,16 @@ struct Plan {
 // fill the GPU several times over.  The FP64 kernel is bound by arithmetic, so
 // finer items (better balance across SMs) pay; the FP32 kernel is bound by
 // memory, where each z-chunk re-reads two halo planes, so it takes fewer.
-// The server plans each request alone with a target of 1 (whole blocks per
-// item): many requests run at once, so each needs no splitting.
+// The server plans each request alone (so its result does not depend on the
+// mix) with kServeTargetItems and z-chunks of at least kServeMinChunk planes:
+// a request running alone still spreads over the GPU, while the halo planes
+// each chunk re-reads stay a bounded share.
 constexpr int64_t kTargetItemsF64 = 4096;
 constexpr int64_t kTargetItemsF32 = 2048;
+constexpr int64_t kServeTargetItems = 304;
+constexpr int64_t kServeMinChunk = 16;
 int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* splits, jacobi_dtype dtype,
-               const jacobi_init* inits, Plan* out, int64_t target_items = 0);
+               const jacobi_init* inits, Plan* out, int64_t target_items = 0, int64_t min_chunk = 2);
 
 // Device block table entries of a plan whose workspace starts at `ws`; block
 // and neighbour ids are offset by `base`; grid_override >= 0 replaces every

@@ -159,7 +159,7 @@ int validate(const serve_s* s, const serve_request* r, Plan* plan) {
   if (r->max_iters < 0 || r->max_iters % s->cfg.check_every)
     return set_error(JACOBI_EINVAL, "max_iters must be a non-negative multiple of check_every (%d)",
                      s->cfg.check_every);
-  int rc = plan_build(1, &r->grid, &r->split, (jacobi_dtype)s->cfg.dtype, &r->init, plan, 1);
+  int rc = plan_build(1, &r->grid, &r->split, (jacobi_dtype)s->cfg.dtype, &r->init, plan, kServeTargetItems, kServeMinChunk);
   if (rc) return rc;
   if ((int64_t)plan->blocks.size() > kBlocksPerSlot || (int64_t)plan->items.size() > kItemsPerSlot)
     return set_error(JACOBI_EINVAL, "request has %zu blocks / %zu work items; a slot holds %lld / %lld",
@@ -184,7 +184,7 @@ int admit(serve_s* s, int si, const Req& q) {
   sl.used = true;
   sl.ticket = q.ticket;
   sl.out = q.r.out;
-  int rc = plan_build(1, &q.r.grid, &q.r.split, (jacobi_dtype)s->cfg.dtype, &q.r.init, &sl.plan, 1);
+  int rc = plan_build(1, &q.r.grid, &q.r.split, (jacobi_dtype)s->cfg.dtype, &q.r.init, &sl.plan, kServeTargetItems, kServeMinChunk);
   if (rc) return rc;
   const Plan& P = sl.plan;
   ENG_CUDA(cudaMallocAsync((void**)&sl.ws, P.bytes, s->stream));
@@ -373,7 +373,7 @@ int engine_loop(serve_s* s) {
         if (free_slot < 0) break;
         Plan probe;
         const serve_request& r = s->queue.front().r;
-        if (plan_build(1, &r.grid, &r.split, (jacobi_dtype)s->cfg.dtype, &r.init, &probe, 1)) break;
+        if (plan_build(1, &r.grid, &r.split, (jacobi_dtype)s->cfg.dtype, &r.init, &probe, kServeTargetItems, kServeMinChunk)) break;
         if (s->bytes_in_use + probe.bytes > s->cfg.hbm_budget_bytes) break;
         q = s->queue.front();
         s->queue.pop_front();

@@ -75,6 +75,68 @@ static int stream_shape(int64_t rx, int64_t ry, size_t elem, uint32_t* stage_byt
   return cw;
 }
 
+// CTAs of one streaming kind resident per SM: registers are capped at 72 per
+// thread by the launch bounds; the ring (4 stages of the largest window)
+// takes shared memory.
+static int64_t stream_ctas_per_sm(int cw, uint32_t stage_bytes) {
+  const int64_t threads = 32 * cw + 32;
+  const int64_t by_regs = 65536 / (threads * 72);
+  const int64_t by_smem = (228 * 1024) / (128 + 4 * (int64_t)stage_bytes + 1024);
+  return std::max<int64_t>(1, std::min<int64_t>({by_regs, by_smem, 32}));
+}
+
+static int64_t device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+      sms > 0)
+    return sms;
+  cudaGetLastError();
+  return 152;
+}
+
+// z-chunk of a handle's work items by a cost model: a launch takes
+// ceil(items / C) waves of C resident CTAs, each item costs its planes plus a
+// fixed pipeline fill of ~2 planes, and in FP32 (bound by memory, not by
+// arithmetic) each chunk's two re-read halo planes cost about one plane of
+// traffic.  C counts the CTAs of the kind with the most units.  Candidates
+// halve from the tallest block down to zmin planes; ties keep the longer chunk.
+// FP32 chunks start at 32 planes at most: on 768^3 in 64^3 blocks, 64-plane
+// chunks measured ~2 % slower than 32 although the model prefers them.
+static int64_t choose_chunk(const Plan& P, const std::vector<int>& warps, const std::vector<int64_t>& chunks,
+                            int64_t maxz, int64_t zmin) {
+  int64_t kind_units[4] = {0, 0, 0, 0};  // tiles, CW 8, 4, 2
+  for (size_t b = 0; b < P.blocks.size(); ++b) {
+    const BlockHost& B = P.blocks[b];
+    const int cw = warps[b];
+    const int k = cw == 0 ? 0 : cw == 8 ? 1 : cw == 4 ? 2 : 3;
+    kind_units[k] += cw ? (B.ry + chunks[b] - 1) / chunks[b] : ((B.extent[0] + TX - 1) / TX) * ((B.extent[1] + TY - 1) / TY);
+  }
+  const int k = (int)(std::max_element(kind_units, kind_units + 4) - kind_units);
+  const int64_t per_sm = k == 0 ? 8 : stream_ctas_per_sm(k == 1 ? 8 : k == 2 ? 4 : 2, P.max_stage);
+  const int64_t C = device_sms() * per_sm;
+  const double halo = P.dtype == JACOBI_F32 ? 1.0 : 0.0;
+  const int64_t z0 = P.dtype == JACOBI_F32 ? std::max<int64_t>(std::min<int64_t>(maxz, 32), zmin) : maxz;
+  int64_t best = z0;
+  double best_cost = 0.0;
+  for (int64_t zc = z0;; zc = (zc + 1) / 2) {
+    int64_t items = 0;
+    for (size_t b = 0; b < P.blocks.size(); ++b) {
+      const BlockHost& B = P.blocks[b];
+      const int64_t per_plane = warps[b] ? (B.ry + chunks[b] - 1) / chunks[b]
+                                         : ((B.extent[0] + TX - 1) / TX) * ((B.extent[1] + TY - 1) / TY);
+      items += per_plane * ((B.extent[2] + zc - 1) / zc);
+    }
+    const double waves = (double)((items + C - 1) / C);
+    const double cost = waves * ((double)zc + 2.0) * (1.0 + halo / (double)zc);
+    if (zc == z0 || cost < best_cost) {
+      best = zc;
+      best_cost = cost;
+    }
+    if (zc <= zmin || (zc + 1) / 2 < zmin) break;
+  }
+  return best;
+}
+
 // Entries of the padded receive slot of face f (see BlockDev), and of the
 // face itself.
 static int64_t face_elems_host(const BlockHost& b, int f) {
@@ -151,10 +213,10 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
     P->grids.push_back(G);
   }
   // Work items.  Blocks that fit the plane-streaming path get one item per
-  // z-chunk; the others one item per TX x TY tile and z-chunk.  The chunk is
-  // the largest power-of-two fraction of the tallest block that still gives
-  // at least `target_items` items (or min_chunk planes, at least 2), so small
-  // problems still spread over many CTAs while large ones stream whole blocks.
+  // row window and z-chunk; the others one item per TX x TY tile and z-chunk.
+  // The chunk is a power-of-two fraction of the tallest block: chosen by the
+  // cost model (choose_chunk) for a handle, or the longest that still gives
+  // at least `target_items` items (down to min_chunk planes, at least 2).
   std::vector<int> warps(P->blocks.size());
   std::vector<int64_t> chunks(P->blocks.size());
   int64_t units = 0, maxz = 0;
@@ -172,10 +234,13 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
     units += cw ? (B.ry + ch - 1) / ch : ((B.extent[0] + TX - 1) / TX) * ((B.extent[1] + TY - 1) / TY);
     maxz = std::max(maxz, B.extent[2]);
   }
-  if (target_items <= 0) target_items = dtype == JACOBI_F64 ? kTargetItemsF64 : kTargetItemsF32;
-  int64_t zc = maxz;
   const int64_t zmin = std::max<int64_t>(min_chunk, 2);
-  while (zc > zmin && (zc + 1) / 2 >= zmin && units * ((maxz + zc - 1) / zc) < target_items) zc = (zc + 1) / 2;
+  int64_t zc = maxz;
+  if (target_items > 0) {
+    while (zc > zmin && (zc + 1) / 2 >= zmin && units * ((maxz + zc - 1) / zc) < target_items) zc = (zc + 1) / 2;
+  } else {
+    zc = choose_chunk(*P, warps, chunks, maxz, zmin);
+  }
   for (GridHost& G : P->grids) {
     G.item_begin = (int64_t)P->items.size();
     for (int64_t b = G.block_begin; b < G.block_end; ++b) {

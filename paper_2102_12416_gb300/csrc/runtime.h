@@ -67,16 +67,13 @@ struct Plan {
   size_t bytes = 0;
 };
 
-// Default work-item target of a handle (target_items <= 0): enough CTAs to
-// fill the GPU several times over.  The FP64 kernel is bound by arithmetic, so
-// finer items (better balance across SMs) pay; the FP32 kernel is bound by
-// memory, where each z-chunk re-reads two halo planes, so it takes fewer.
-// The server plans each request alone (so its result does not depend on the
-// mix) with kServeTargetItems and z-chunks of at least kServeMinChunk planes:
-// a request running alone still spreads over the GPU, while the halo planes
-// each chunk re-reads stay a bounded share.
-constexpr int64_t kTargetItemsF64 = 4096;
-constexpr int64_t kTargetItemsF32 = 2048;
+// With target_items <= 0 (a handle) the z-chunk comes from a cost model of
+// waves, per-item pipeline fill and halo re-reads; with target_items > 0 it is
+// the longest chunk that still gives that many items.  The server plans each
+// request alone (so its result does not depend on the mix) with
+// kServeTargetItems and z-chunks of at least kServeMinChunk planes: a request
+// running alone still spreads over the GPU, while the halo planes each chunk
+// re-reads stay a bounded share.
 constexpr int64_t kServeTargetItems = 304;
 constexpr int64_t kServeMinChunk = 16;
 int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* splits, jacobi_dtype dtype,

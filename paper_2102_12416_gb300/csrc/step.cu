@@ -539,7 +539,9 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, StreamShape<CW>::min
       for (; q < nplanes; ++q) {
         const int st = q % S, fill = q / S;
         if (fill > 0 && !mbar_wait(empty + st, (uint32_t)(fill - 1) & 1u, a.err, a.wait_ns)) break;
-        fence_proxy_async();
+        // No proxy fence: within one launch the bulk copies read only the
+        // parity-p state and slots, which earlier launches wrote (a launch
+        // boundary orders them); this launch writes parity p ^ 1 only.
         issue_plane<T>(B, p, w.z0, nplanes, q, w.ya, w.yb, L, stages + (size_t)st * L.bytes, full + st);
       }
       if (q < nplanes) {

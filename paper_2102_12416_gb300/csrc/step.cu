@@ -247,6 +247,7 @@ struct PlaneView {
   int64_t pitch;
   T* V;                    // new iterate
   const BlockDev* B;       // for the send pointers, read by edge threads only
+  void* const* ss;         // the six send slots copied to shared memory, or null
 };
 template <typename T>
 __device__ __forceinline__ PlaneView<T> plane_view(const BlockDev& B, int p) {
@@ -260,11 +261,14 @@ __device__ __forceinline__ PlaneView<T> plane_view(const BlockDev& B, int p) {
   v.pitch = B.plane_pitch;
   v.V = (T*)B.u[p ^ 1];
   v.B = &B;
+  v.ss = nullptr;
   return v;
 }
-// Neighbour receive slot of face f for the new iterate (read-only path).
+// Neighbour receive slot of face f for the new iterate: from the CTA's
+// shared-memory copy when there is one, else through the read-only path.
 template <typename T>
 __device__ __forceinline__ T* send_slot(const PlaneView<T>& O, int f) {
+  if (O.ss) return (T*)O.ss[f];
   return (T*)__ldg((const unsigned long long*)&O.B->send[f][O.pn]);
 }
 
@@ -309,6 +313,12 @@ __device__ __forceinline__ double stream_plane(const PlaneView<T>& O, int k, int
   V16<T>::load(j0 > 0 ? Pc + (j0 - 1) * rx + i0 : Gym + i0, top);
   V16<T>::load(j0 + RY < ny ? Pc + (j0 + RY) * rx + i0 : Gyp + i0, bot);
   double acc = 0.0;
+  // x-face values of this thread's column over its RY rows: the first column
+  // gives the xm face, else the last column the xp face; stored as whole
+  // 16-byte vectors after the rows (rows are consecutive in an x slot).
+  // A column that is both (one vector wide) stores its xp face row by row.
+  T xe[RY];
+  const bool xfirst = i0 == 0, xlast = ql < VEC;
 #pragma unroll
   for (int r = 0; r < RY; ++r) {
     const int j = j0 + r;
@@ -331,23 +341,22 @@ __device__ __forceinline__ double stream_plane(const PlaneView<T>& O, int k, int
         acc += (!RAG || (q <= ql && j < ny)) ? e2 : 0.0;
       }
     }
+    if ((MODE & kWrite) && (MODE & kPack)) {
+      T last = v[VEC - 1];
+      if (RAG) {
+#pragma unroll
+        for (int q = 0; q < VEC - 1; ++q)
+          if (q == ql) last = v[q];
+      }
+      xe[r] = xfirst ? v[0] : last;
+      if (xfirst && xlast && (!RAG || j < ny)) {
+        T* d = send_slot(O, XP);
+        if (d) d[(int64_t)k * ry + j] = last;
+      }
+    }
     if ((MODE & kWrite) && (!RAG || j < ny)) {
       V16<T>::store(V + j * rx + i0, v);
       if (MODE & kPack) {
-        if (i0 == 0) {
-          T* d = send_slot(O, XM);
-          if (d) d[(int64_t)k * ry + j] = v[0];
-        }
-        if (ql < VEC) {
-          T* d = send_slot(O, XP);
-          T last = v[VEC - 1];
-          if (RAG) {
-#pragma unroll
-            for (int q = 0; q < VEC - 1; ++q)
-              if (q == ql) last = v[q];
-          }
-          if (d) d[(int64_t)k * ry + j] = last;
-        }
         if (j == 0) {
           T* d = send_slot(O, YM);
           if (d) V16<T>::store(d + (int64_t)k * rx + i0, v);
@@ -364,6 +373,19 @@ __device__ __forceinline__ double stream_plane(const PlaneView<T>& O, int k, int
           T* d = send_slot(O, ZP);
           if (d) V16<T>::store(d + j * rx + i0, v);
         }
+      }
+    }
+  }
+  if ((MODE & kWrite) && (MODE & kPack) && (xfirst || xlast)) {
+    T* d = send_slot(O, xfirst ? XM : XP);
+    if (d) {
+      T* x = d + (int64_t)k * ry + j0;  // 16-byte aligned: ry and j0 are multiples of 4
+#pragma unroll
+      for (int r = 0; r < RY; r += VEC) {
+        T w[VEC];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) w[q] = xe[r + q];
+        V16<T>::store(x + r, w);
       }
     }
   }
@@ -523,6 +545,12 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, StreamShape<CW>::min
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nplanes = w.z1 - w.z0 + 2;  // planes z0-1 .. z1
   const StageLayout L = stage_layout<T>(B, w.ya, w.yb);
+  // The send slots in shared memory save the consumers a dependent global
+  // load before each face store.  Same-box A/B: faster in every variant but
+  // the FP64 ones with fewer than 8 consumer warps, where ptxas then spills.
+  constexpr bool kSendTable = !(sizeof(T) == 8 && CW < 8);
+  __shared__ void* s_send[6];
+  if (kSendTable && tid < 6) s_send[tid] = B.send[tid][p ^ 1];
   if (tid == 0) {
     for (int st = 0; st < S; ++st) {
       mbar_init(full + st, 1);
@@ -556,7 +584,8 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, StreamShape<CW>::min
   } else {
     // ---- consumers ----
     const bool emu = sizeof(T) == 8 && a.emu && a.norms && a.norms[B.grid].emu_bad == 0u;
-    const PlaneView<T> O = plane_view<T>(B, p);
+    PlaneView<T> O = plane_view<T>(B, p);
+    if (kSendTable) O.ss = s_send;
     const int txv = O.rx / VEC;
     const int tx = tid % txv, j0 = w.ya + (tid / txv) * RY;
     const bool active = j0 < w.yb;

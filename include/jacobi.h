@@ -147,7 +147,8 @@ typedef struct {
   int32_t path;
   int64_t halo_bytes_per_iter; /* face payload moved per iteration (bytes) */
   size_t workspace_bytes;
-  int32_t stages;        /* ring depth of the plane-streaming kernels          */
+  int32_t stages;        /* ring depth of the persistent kernel (the per-step
+                            streaming kernels use 4)                          */
   int32_t item_kinds;    /* kernel variants launched per iteration (fused paths) */
   int32_t fp64_int_adds; /* FP64 adds per update run on the integer pipe (0 or 3)
                             for grids inside the integer adder's domain         */
@@ -215,8 +216,8 @@ int jacobi_block(const jacobi_t* h, int64_t block, jacobi_block_info* out);
 int jacobi_set_path(jacobi_t* h, int32_t path);
 
 /* Autotuner (the library's addition): times every candidate step
- * configuration -- path FUSED/GRAPH/PERSISTENT x ring depth 3..6 of the
- * plane-streaming kernels, where it fits shared memory -- for iters_per_trial
+ * configuration -- path FUSED/GRAPH, and PERSISTENT x ring depth 3..6 where
+ * it fits shared memory -- for iters_per_trial
  * iterations on a scratch handle with the same grids, splits and dtype (the
  * handle's own state is untouched), then applies the fastest to `h`.  All
  * candidates give bit-identical iterates.  When the environment variable

@@ -69,7 +69,7 @@ static int stream_shape(int64_t rx, int64_t ry, size_t elem, uint32_t* stage_byt
   if (ch <= 0) return 0;
   ch = std::min(ch, ry);
   const uint64_t stage = ((uint64_t)((ch + 2) * rx + 2 * ch + 2 * rx) * elem + 127) / 128 * 128;
-  if (128 + 4 * stage > (uint64_t)kMaxStepSmem) return 0;
+  if (128 + kStreamStages * stage > (uint64_t)kMaxStepSmem) return 0;
   *stage_bytes = (uint32_t)stage;
   *chunk = ch;
   return cw;
@@ -466,8 +466,8 @@ StepLaunch step_args(jacobi_t* h, int64_t it, bool all_items) {
   a.it = it;
   a.partials = h->d_partials;
   a.dtype = h->plan.dtype;
-  a.stages = h->stages;
-  a.smem = 128 + h->stages * (int32_t)h->plan.max_stage;
+  a.stages = kStreamStages;
+  a.smem = 128 + kStreamStages * (int32_t)h->plan.max_stage;
   a.err = h->d_err;
   a.wait_ns = h->wait_ns;
   a.norms = h->d_norms;
@@ -801,8 +801,9 @@ int jacobi_create_batch(int64_t n_grids, const jacobi_dim3* grids, const jacobi_
     const double ms = atof(w);
     if (ms > 0) h->wait_ns = (uint64_t)(ms * 1e6);
   }
-  // Ring depth of the plane-streaming path: four stages keep one plane in
-  // flight beyond the three a consumer reads (the autotuner may pick more).
+  // Ring depth of the persistent kernel's plane streaming: four stages keep
+  // one plane in flight beyond the three a consumer reads (the autotuner may
+  // pick another); the per-step kernels always use kStreamStages.
   h->stages = 4;
   if (const char* em = getenv("JACOBI_FP64_EMU")) h->fp64_emu = atoi(em) != 0 ? 1 : 0;
   if (const char* st = getenv("JACOBI_STAGES")) {
@@ -941,6 +942,8 @@ extern "C" int jacobi_autotune(jacobi_t* h, int64_t iters_per_trial, void* strea
     const int32_t paths[3] = {JACOBI_PATH_GRAPH, JACOBI_PATH_PERSISTENT, JACOBI_PATH_FUSED};
     for (int32_t path : paths) {
       for (int32_t st = 3; st <= 6; ++st) {
+        // the ring depth is a choice of the persistent kernel only
+        if (path != JACOBI_PATH_PERSISTENT && st != kStreamStages) continue;
         if (128 + st * (int64_t)P.max_stage > kMaxStepSmem) continue;
         if (P.max_stage == 0 && st != 3) continue;  // no plane-streamed blocks: the depth is irrelevant
         t->stages = st;

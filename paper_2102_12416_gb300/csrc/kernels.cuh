@@ -32,6 +32,11 @@ constexpr int kMaxStepSmem = 227 * 1024 - 1024;  // 1 KB left for static shared 
 // 8, 4, 2 consumer warps; 4, 5, 6 = the same for ragged blocks.  Each kind
 // runs its own kernel variant.
 constexpr int kItemKinds = 7;
+// Ring depth of the per-step plane-streaming kernels: a compile-time 4 (the
+// stage index is a mask, and 4 measured best for every block shape; the
+// planner only streams blocks whose 4-stage ring fits shared memory).  The
+// persistent kernel's ring depth stays a run-time choice.
+constexpr int kStreamStages = 4;
 constexpr int kItemRagged = 16;
 __host__ __device__ inline bool item_ragged(const WorkItem& w) { return (w.y0 & kItemRagged) != 0; }
 __host__ __device__ inline int item_kind(const WorkItem& w) {

@@ -287,8 +287,8 @@ int run_round(serve_s* s) {
   a.grids = s->d_grids;
   a.partials = s->d_partials;
   a.dtype = s->cfg.dtype;
-  a.stages = s->stages;
-  a.smem = 128 + s->stages * (int32_t)s->max_stage;
+  a.stages = kStreamStages;
+  a.smem = 128 + kStreamStages * (int32_t)s->max_stage;
   a.err = s->d_err;
   a.wait_ns = 1000000000ull;
   a.norms = s->d_norms;

@@ -150,8 +150,9 @@ typedef struct {
   int32_t stages;        /* ring depth of the persistent kernel (the per-step
                             streaming kernels use 4)                          */
   int32_t item_kinds;    /* kernel variants launched per iteration (fused paths) */
-  int32_t fp64_int_adds; /* FP64 adds per update run on the integer pipe (0 or 3)
-                            for grids inside the integer adder's domain         */
+  int32_t fp64_int_adds; /* neighbour pair sums per update that may run on the
+                            integer pipe (0 or 3) for grids inside the integer
+                            adder's domain; the kernels send most of them there */
   int32_t pad_;
 } jacobi_info_t;
 

@@ -195,6 +195,18 @@ __device__ __forceinline__ T nsum(T xm, T xp, T ym, T yp, T zm, T zp) {
   return radd(radd(radd(xm, xp), radd(ym, yp)), radd(zm, zp));
 }
 
+// nsum with the z pair on the FP64 pipe (bit-identical: both adders round
+// to nearest-even).
+template <typename T, bool EMU>
+__device__ __forceinline__ T nsum_zn(T xm, T xp, T ym, T yp, T zm, T zp) {
+  if (EMU) {
+    const double sx = dadd_nn((double)xm, (double)xp), sy = dadd_nn((double)ym, (double)yp),
+                 sz = __dadd_rn((double)zm, (double)zp);
+    return (T)__dadd_rn(__dadd_rn(sx, sy), sz);
+  }
+  return radd(radd(radd(xm, xp), radd(ym, yp)), radd(zm, zp));
+}
+
 // Shared-memory stage of one plane of a padded row window [ya, yb) of block
 // B: rows ra..rb-1 of the plane (the window plus one neighbour row on each
 // side that exists), then the x ghosts of the window's rows (xm, xp), then the
@@ -340,7 +352,11 @@ __device__ __forceinline__ double stream_plane(const PlaneView<T>& O, int k, int
     for (int q = 0; q < VEC; ++q) {
       const T xm = q == 0 ? left : c[r][q > 0 ? q - 1 : 0];
       const T xp = q == VEC - 1 ? right : c[r][q < VEC - 1 ? q + 1 : 0];
-      const T s = nsum<T, EMU>(xm, xp, ym[q], yp[q], zm[q], zp[q]);
+      // FP64: the z pair of 2 of a thread's 8 points goes to the FP64 pipe,
+      // shifting work off the busier integer pipe (same-box A/B +0.5 % on
+      // 64^3 blocks, +1.9 % on 32^3; 3 or 4 of 8 gained less).
+      const T s = (q == VEC - 1 && r < 2) ? nsum_zn<T, EMU>(xm, xp, ym[q], yp[q], zm[q], zp[q])
+                                          : nsum<T, EMU>(xm, xp, ym[q], yp[q], zm[q], zp[q]);
       v[q] = rmul(s, C6<T>::v);
       if (MODE & kResid) {
         const double e2 = resid2<T>(xm, xp, ym[q], yp[q], zm[q], zp[q], s, c[r][q]);

@@ -154,6 +154,20 @@ def dist_setup(args):
     return world, rank, local
 
 
+def replica_totals(dist, device, local_ms, local_units):
+    """Whole-job figures of independent per-GPU replicas (weak scaling, no
+    data-path collective): the time is the slowest rank's, the work the sum
+    over ranks.  With dist None (one process) the local figures."""
+    if dist is None:
+        return float(local_ms), float(local_units)
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([local_units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def workload_config(name, grids, splits, dtype, iters, path):
     elem = 8 if dtype == "f64" else 4
     points = sum(g[0] * g[1] * g[2] for g in grids)
@@ -499,12 +513,9 @@ def run_ours(args):
     clk = clocks.stop()
     total_ms = ev[0].elapsed_time(ev[1])
     stencil_ms = sum(ev[2 + 2 * k].elapsed_time(ev[3 + 2 * k]) for k in range(args.steps))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, job_lups = replica_totals(dist, "cuda", total_ms, n_points * iters * args.steps)
     ms_per_step = total_ms / args.steps
-    value = world * n_points * iters * args.steps / (total_ms * 1e-3) / 1e9
+    value = job_lups / (total_ms * 1e-3) / 1e9
     kinds = s.launch_kinds()
     launches = args.steps * (iters * (kinds if path_used != "persistent" else 1) + kinds + 1)
 
@@ -563,12 +574,8 @@ def run_ours(args):
             jg.jacobi_copy_out(s.h, gi, h_out[gi].data_ptr(), False, jg.JACOBI_LAYOUT_INTERIOR, stream)
     e1.record(stream)
     e1.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": world * n_points * iters * e2e_steps / (e2e_ms * 1e-3) / 1e9, "unit": "GLUP/s",
+    e2e_ms, e2e_lups = replica_totals(dist, "cuda", e0.elapsed_time(e1), n_points * iters * e2e_steps)
+    e2e = {"value": e2e_lups / (e2e_ms * 1e-3) / 1e9, "unit": "GLUP/s",
            "h2d_bytes_per_step": sum(x.numel() * x.element_size() for x in h_in),
            "d2h_bytes_per_step": sum(x.numel() * x.element_size() for x in h_out) + 16 * len(grids),
            "steps": e2e_steps}

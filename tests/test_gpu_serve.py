@@ -122,3 +122,48 @@ def test_rejects_bad_requests():
             jg.serve_poll(s, 12345)
     finally:
         jg.serve_destroy(s)
+
+
+def _bench_stream(indices, n=400):
+    """Requests of the serving benchmark's own stream (FP32 state, 32^3
+    blocks, noisy linear boundary), by index."""
+    import bench
+    c = bench.SERVE_CFG
+    reqs = J.serving_requests(n)
+    return [(reqs[i]["grid"], ("shape", c["block"]),
+             dict(bc="linear_noise", bc_seed=reqs[i]["seed"], noise_amp=c["noise_amp"], interior="zero"))
+            for i in indices], c
+
+
+def test_bench_stream_small_requests_vs_oracle(oracle_mod):
+    """The benchmark stream's requests with every side <= 56, served together
+    with bench settings, equal the FP32 oracle's solve: same iterations and
+    status, bit-identical final iterate, residual within 1e-12."""
+    reqs = J.serving_requests(400)
+    idx = [i for i, r in enumerate(reqs) if max(r["grid"]) <= 56][:8]
+    sample, c = _bench_stream(idx)
+    res, outs, _ = _serve(sample, "f32", c["tol"], c["cap"], c["check_every"], slots=32)
+    for (g, sp, ini), r, o in zip(sample, res, outs):
+        want, k, orel, ost = oracle_mod.solve(J.initial_grid(*g, dtype=np.float32, **ini), c["tol"], c["cap"],
+                                              c["check_every"])
+        assert (r.iters, r.status) == (k, ost), g
+        assert abs(r.rel - orel) <= RES_TOL * orel, g
+        assert np.array_equal(o, J.interior_of(want)), g
+
+
+def test_bench_stream_large_requests_vs_standalone():
+    """The stream's larger requests (every side >= 80), served together, equal
+    standalone solves of the same grids on a handle (whose iterates the
+    parity tests pin to the oracle): same iterations and status, bit-identical
+    final iterate, residual within 1e-12."""
+    reqs = J.serving_requests(200)
+    idx = [i for i, r in enumerate(reqs) if min(r["grid"]) >= 80][:5]
+    sample, c = _bench_stream(idx, 200)
+    res, outs, _ = _serve(sample, "f32", c["tol"], c["cap"], c["check_every"], slots=32)
+    for (g, sp, ini), r, o in zip(sample, res, outs):
+        with jg.Jacobi3D(g, sp, "f32", ini) as h:
+            it, rel, st = h.solve(c["tol"], c["cap"], c["check_every"])
+            alone = h.copy_out()
+        assert (r.iters, r.status) == (it[0], st[0]), g
+        assert abs(r.rel - rel[0]) <= RES_TOL * rel[0], g
+        assert np.array_equal(o, alone), g

@@ -378,3 +378,25 @@ def test_persistent_wait_times_out(monkeypatch):
     with _solver((32, 32, 32), ("count", (2, 2, 2)), "f64", None, "persistent") as s:
         s.step(3)
         s.sync()
+
+
+@pytest.mark.parametrize("dtype,nx", [("f32", 1030), ("f64", 515)])
+@pytest.mark.parametrize("path", ["fused", "graph", "persistent", "explicit"])
+def test_wide_rows_take_the_tile_kernel(oracle_mod, dtype, nx, path):
+    """Rows wider than one CTA can stream (more than 256 16-byte vectors) go
+    to the tile kernel, alone and next to streamed blocks; iterates stay
+    bit-exact, faces are packed and the residual matches."""
+    grid = (nx + 40, 11, 9)
+    init = dict(bc="uniform", bc_seed=51, interior="uniform", interior_seed=52)
+    npdt = np.float64 if dtype == "f64" else np.float32
+    u0 = J.initial_grid(*grid, dtype=npdt, **init)
+    want = oracle_mod.jacobi(u0, 6)
+    rn, _, rel = oracle_mod.residual(want)
+    # one wide block (tiles) beside a 40-wide one (streamed), split in z too
+    with _solver(grid, ("shape", (nx, 11, 5)), dtype, init, path) as s:
+        assert s.launch_kinds() >= 2
+        s.step(6)
+        got = s.copy_out()
+        grel, gabs = s.residual()
+    assert np.array_equal(got, J.interior_of(want))
+    assert abs(gabs[0] - rn) <= RES_TOL * rn and abs(grel[0] - rel) <= RES_TOL * rel

@@ -234,7 +234,9 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
     units += cw ? (B.ry + ch - 1) / ch : ((B.extent[0] + TX - 1) / TX) * ((B.extent[1] + TY - 1) / TY);
     maxz = std::max(maxz, B.extent[2]);
   }
-  const int64_t zmin = std::max<int64_t>(min_chunk, 2);
+  // the cost model may go down to single planes (a small problem that fits
+  // one wave); the item-target rule stops at 2
+  const int64_t zmin = std::max<int64_t>(min_chunk, target_items > 0 ? 2 : 1);
   int64_t zc = maxz;
   if (target_items > 0) {
     while (zc > zmin && (zc + 1) / 2 >= zmin && units * ((maxz + zc - 1) / zc) < target_items) zc = (zc + 1) / 2;

@@ -77,7 +77,7 @@ struct Plan {
 constexpr int64_t kServeTargetItems = 304;
 constexpr int64_t kServeMinChunk = 16;
 int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* splits, jacobi_dtype dtype,
-               const jacobi_init* inits, Plan* out, int64_t target_items = 0, int64_t min_chunk = 2);
+               const jacobi_init* inits, Plan* out, int64_t target_items = 0, int64_t min_chunk = 1);
 
 // Device block table entries of a plan whose workspace starts at `ws`; block
 // and neighbour ids are offset by `base`; grid_override >= 0 replaces every

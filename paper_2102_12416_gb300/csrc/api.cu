@@ -243,6 +243,9 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
   } else {
     zc = choose_chunk(*P, warps, chunks, maxz, zmin);
   }
+  P->zchunk = zc;
+  P->n_units = 0;
+  for (const BlockHost& B : P->blocks) P->n_units += (B.extent[2] + zc - 1) / zc;
   for (GridHost& G : P->grids) {
     G.item_begin = (int64_t)P->items.size();
     for (int64_t b = G.block_begin; b < G.block_end; ++b) {
@@ -292,11 +295,14 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
   P->off_inits = take(ng * sizeof(InitDev));
   P->off_gids = take(ng * sizeof(int32_t));
   P->off_partials = take(ni * sizeof(double));
-  P->off_progress = take(nb * sizeof(int64_t));
+  const int64_t nu = P->n_units;
+  P->off_progress = take(nu * sizeof(int64_t));
   P->off_err = take(64);
   P->off_stage_tab = take(nb * 6 * sizeof(void*));
-  P->off_pblock_items = take((nb + 1) * sizeof(int32_t));
-  P->off_pblock_ids = take(nb * sizeof(int32_t));
+  P->off_punit_items = take((nu + 1) * sizeof(int32_t));
+  P->off_punit_ids = take(nu * sizeof(int32_t));
+  P->off_pdep_off = take((nu + 1) * sizeof(int32_t));
+  P->off_pdep_ids = take(8 * nu * sizeof(int32_t));
   const size_t per16 = 32;  // plane pitch rounded to 32 elements
   for (auto& B : P->blocks) {
     B.pitch = (int64_t)align_up((size_t)(B.rx * B.ry), per16);
@@ -393,7 +399,7 @@ int upload_tables(jacobi_t* h, cudaStream_t s) {
   JGB_CUDA(cudaMemcpyAsync(h->d_stage_tab, stab.data(), stab.size() * sizeof(void*), cudaMemcpyHostToDevice, s));
   JGB_CUDA(cudaMemcpyAsync(h->d_grids, h->h_grids, ng * sizeof(GridDev), cudaMemcpyHostToDevice, s));
   JGB_CUDA(cudaMemsetAsync(h->d_norms, 0, ng * sizeof(GridNorm), s));
-  JGB_CUDA(cudaMemsetAsync(h->d_progress, 0, nb * sizeof(int64_t), s));
+  JGB_CUDA(cudaMemsetAsync(h->d_progress, 0, P.n_units * sizeof(int64_t), s));
   JGB_CUDA(cudaMemsetAsync(h->d_err, 0, 64, s));
   // The host arrays above are pageable, so each copy has been staged before
   // cudaMemcpyAsync returned; they may go out of scope now.
@@ -409,22 +415,48 @@ int refresh_active(jacobi_t* h, cudaStream_t s) {
   }
   const Plan& P = h->plan;
   h->active_items.clear();
-  h->active_blocks.clear();
-  h->active_block_items.clear();
+  h->active_units.clear();
+  h->active_unit_items.clear();
+  h->active_dep_off.clear();
+  h->active_deps.clear();
   h->active_grids.clear();
+  // Persistent-kernel units: the z-chunks of each block (items are ordered by
+  // z-chunk within a block).  Unit (b, c) at iteration it needs iteration
+  // it - 1 finished by the units it shares data with, both ways (reads of
+  // what they write, writes of what they read): chunks c - 1 and c + 1 of b
+  // (halo planes), chunk c of the x and y neighbours (faces over the same
+  // planes; blocks side by side share nz, hence the chunking) and the facing
+  // chunk of the z neighbours.  The relation is symmetric.
+  std::vector<int64_t> unit0(P.blocks.size() + 1, 0);
+  for (size_t b = 0; b < P.blocks.size(); ++b)
+    unit0[b + 1] = unit0[b] + (P.blocks[b].extent[2] + P.zchunk - 1) / P.zchunk;
+  auto chunks = [&](int64_t b) { return unit0[b + 1] - unit0[b]; };
   for (size_t g = 0; g < P.grids.size(); ++g) {
     const GridHost& G = P.grids[g];
     if (!G.active) continue;
     h->active_grids.push_back((int32_t)g);
     for (int64_t b = G.block_begin; b < G.block_end; ++b) {
       if (b == h->drop_block && h->path == JACOBI_PATH_PERSISTENT) continue;  // injected fault
-      h->active_blocks.push_back((int32_t)b);
-      h->active_block_items.push_back((int32_t)h->active_items.size());
       const BlockHost& B = P.blocks[b];
-      for (int64_t q = B.item_begin; q < B.item_end; ++q) h->active_items.push_back(P.items[q]);
+      const int64_t nc = chunks(b);
+      const int64_t per_chunk = (B.item_end - B.item_begin) / nc;
+      for (int64_t c = 0; c < nc; ++c) {
+        h->active_units.push_back((int32_t)(unit0[b] + c));
+        h->active_unit_items.push_back((int32_t)h->active_items.size());
+        for (int64_t q = B.item_begin + c * per_chunk; q < B.item_begin + (c + 1) * per_chunk; ++q)
+          h->active_items.push_back(P.items[q]);
+        h->active_dep_off.push_back((int32_t)h->active_deps.size());
+        if (c > 0) h->active_deps.push_back((int32_t)(unit0[b] + c - 1));
+        if (c + 1 < nc) h->active_deps.push_back((int32_t)(unit0[b] + c + 1));
+        for (int f = 0; f < 4; ++f)
+          if (B.nbr[f] >= 0) h->active_deps.push_back((int32_t)(unit0[B.nbr[f]] + c));
+        if (c == 0 && B.nbr[ZM] >= 0) h->active_deps.push_back((int32_t)(unit0[B.nbr[ZM]] + chunks(B.nbr[ZM]) - 1));
+        if (c == nc - 1 && B.nbr[ZP] >= 0) h->active_deps.push_back((int32_t)unit0[B.nbr[ZP]]);
+      }
     }
   }
-  h->active_block_items.push_back((int32_t)h->active_items.size());
+  h->active_unit_items.push_back((int32_t)h->active_items.size());
+  h->active_dep_off.push_back((int32_t)h->active_deps.size());
   // The same items grouped by kind (stable), for one kernel variant per kind.
   h->kind_items.clear();
   for (int k = 0; k < kItemKinds; ++k) {
@@ -439,11 +471,14 @@ int refresh_active(jacobi_t* h, cudaStream_t s) {
     JGB_CUDA(cudaMemcpyAsync(h->d_kind, h->kind_items.data(), h->kind_items.size() * sizeof(WorkItem),
                              cudaMemcpyHostToDevice, s));
   }
-  if (!h->active_blocks.empty()) {
-    JGB_CUDA(cudaMemcpyAsync(h->d_pblock_ids, h->active_blocks.data(), h->active_blocks.size() * sizeof(int32_t),
-                             cudaMemcpyHostToDevice, s));
-    JGB_CUDA(cudaMemcpyAsync(h->d_pblock_items, h->active_block_items.data(),
-                             h->active_block_items.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  if (!h->active_units.empty()) {
+    auto up = [&](int32_t* d, const std::vector<int32_t>& v) {
+      return cudaMemcpyAsync(d, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    };
+    JGB_CUDA(up(h->d_punit_ids, h->active_units));
+    JGB_CUDA(up(h->d_punit_items, h->active_unit_items));
+    JGB_CUDA(up(h->d_pdep_off, h->active_dep_off));
+    if (!h->active_deps.empty()) JGB_CUDA(up(h->d_pdep_ids, h->active_deps));
   }
   // start_iter of every grid (changes when grids are frozen / re-activated)
   for (size_t g = 0; g < P.grids.size(); ++g) {
@@ -546,9 +581,11 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
   PersistLaunch a;
   a.blocks = h->d_blocks;
   a.items = h->d_active;
-  a.block_items = h->d_pblock_items;
-  a.block_ids = h->d_pblock_ids;
-  a.n_blocks = (int32_t)h->active_blocks.size();
+  a.unit_items = h->d_punit_items;
+  a.unit_ids = h->d_punit_ids;
+  a.dep_off = h->d_pdep_off;
+  a.dep_ids = h->d_pdep_ids;
+  a.n_units = (int32_t)h->active_units.size();
   a.grids = h->d_grids;
   a.it0 = it0;
   a.n_iters = n;
@@ -563,7 +600,7 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
   a.norms = h->d_norms;
   a.emu = h->fp64_emu;
   a.pad_ = 0;
-  const int ctas = std::min(maxc, a.n_blocks);
+  const int ctas = std::min(maxc, a.n_units);
   JGB_CUDA(launch_persistent(a, ctas, s));
   return JACOBI_OK;
 }
@@ -797,8 +834,10 @@ int jacobi_create_batch(int64_t n_grids, const jacobi_dim3* grids, const jacobi_
   h->d_progress = (int64_t*)(h->ws + P.off_progress);
   h->d_err = (uint32_t*)(h->ws + P.off_err);
   h->d_stage_tab = (void**)(h->ws + P.off_stage_tab);
-  h->d_pblock_items = (int32_t*)(h->ws + P.off_pblock_items);
-  h->d_pblock_ids = (int32_t*)(h->ws + P.off_pblock_ids);
+  h->d_punit_items = (int32_t*)(h->ws + P.off_punit_items);
+  h->d_punit_ids = (int32_t*)(h->ws + P.off_punit_ids);
+  h->d_pdep_off = (int32_t*)(h->ws + P.off_pdep_off);
+  h->d_pdep_ids = (int32_t*)(h->ws + P.off_pdep_ids);
   if (const char* w = getenv("JACOBI_WAIT_MS")) {
     const double ms = atof(w);
     if (ms > 0) h->wait_ns = (uint64_t)(ms * 1e6);

@@ -119,14 +119,16 @@ cudaError_t launch_gather(const BlockDev* blocks, const BlockGeom* geom, int32_t
 // Persistent path: one cooperative launch runs n_iters iterations.
 struct PersistLaunch {
   const BlockDev* blocks;
-  const WorkItem* items;       // active items, grouped by block
-  const int32_t* block_items;  // per active block: first item index (n_blocks + 1 entries)
-  const int32_t* block_ids;    // active block ids
-  int32_t n_blocks;            // active blocks
+  const WorkItem* items;       // active items, grouped by unit (block, z-chunk)
+  const int32_t* unit_items;   // per active unit: first item index (n_units + 1 entries)
+  const int32_t* unit_ids;     // per active unit: its unit id (index into progress)
+  const int32_t* dep_off;      // per active unit: first dependency (n_units + 1 entries)
+  const int32_t* dep_ids;      // unit ids that must have finished the previous iteration
+  int32_t n_units;             // active units
   const GridDev* grids;
   int64_t it0;
   int64_t n_iters;
-  int64_t* progress;           // per block: iterations completed (absolute)
+  int64_t* progress;           // per unit: iterations completed (absolute)
   uint32_t* err;
   uint64_t wait_ns;
   double* partials;

@@ -61,9 +61,11 @@ struct Plan {
   int64_t n_points = 0;
   int64_t halo_elems = 0;  // face elements moved per iteration (internal faces)
   uint32_t max_stage = 0;  // largest ring stage (bytes) of a plane-streamed block
+  int64_t zchunk = 1;      // planes per z-chunk (the last chunk of a block may be shorter)
+  int64_t n_units = 0;     // persistent-kernel units: (block, z-chunk) pairs
   // byte offsets into the workspace
   size_t off_blocks, off_geom, off_items, off_active, off_kind, off_grids, off_norms, off_inits, off_gids, off_partials,
-      off_progress, off_err, off_stage_tab, off_pblock_items, off_pblock_ids;
+      off_progress, off_err, off_stage_tab, off_punit_items, off_punit_ids, off_pdep_off, off_pdep_ids;
   size_t bytes = 0;
 };
 
@@ -112,13 +114,19 @@ struct jacobi_s {
   int64_t* d_progress = nullptr;
   uint32_t* d_err = nullptr;
   void** d_stage_tab = nullptr;
-  int32_t* d_pblock_items = nullptr;
-  int32_t* d_pblock_ids = nullptr;
+  int32_t* d_punit_items = nullptr;
+  int32_t* d_punit_ids = nullptr;
+  int32_t* d_pdep_off = nullptr;
+  int32_t* d_pdep_ids = nullptr;
 
   // host mirrors
   std::vector<jgb::WorkItem> active_items;
-  std::vector<int32_t> active_blocks;       // block ids of active grids (item-grouped)
-  std::vector<int32_t> active_block_items;  // n_active_blocks + 1 offsets into active_items
+  // persistent kernel: active units (block, z-chunk) in item order, their item
+  // ranges in active_items and their dependency lists (unit ids, CSR)
+  std::vector<int32_t> active_units;        // unit ids
+  std::vector<int32_t> active_unit_items;   // n_active_units + 1 offsets into active_items
+  std::vector<int32_t> active_dep_off;      // n_active_units + 1 offsets into active_deps
+  std::vector<int32_t> active_deps;
   std::vector<int32_t> active_grids;
   std::vector<jgb::WorkItem> kind_items;        // active items grouped by kind
   int32_t kind_off[jgb::kItemKinds + 1] = {};

@@ -650,13 +650,17 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, StreamShape<CW>::min
 }
 
 // ---------------------------------------------------------------------------
-// Persistent kernel: CTA c owns active blocks c, c + G, c + 2G, ... for all
-// n_iters iterations.  Before block b computes iteration it (> it0) its CTA
-// acquire-waits until every neighbour's progress flag reaches it (the
-// neighbour finished iteration it - 1, so its faces of u_it are in b's slots
-// and it no longer reads the slots b is about to overwrite); after b's sweep
-// the CTA release-stores progress[b] = it + 1.  Waits are bounded: on expiry
-// the error word is set and every CTA leaves at its next wait.
+// Persistent kernel: the work is split into units, the z-chunks of the blocks
+// (a unit's items are its row windows or tiles); CTA c owns active units c,
+// c + G, c + 2G, ... for all n_iters iterations.  Before unit u computes
+// iteration it (> it0) its CTA acquire-waits until the progress flag of every
+// unit it shares data with reaches it (that unit finished iteration it - 1:
+// its faces and halo planes of u_it are written, and it no longer reads what
+// u is about to overwrite); after u's sweep the CTA release-stores
+// progress[u] = it + 1.  The host lists each unit's partners (its block's
+// adjacent chunks, the same chunk of the x and y neighbours, the facing chunk
+// of the z neighbours).  Waits are bounded: on expiry the error word is set and
+// every CTA leaves at its next wait.
 // Proxy fences order the generic stores of neighbours (and of this CTA's
 // previous iteration) before the bulk copies that read them.
 // ---------------------------------------------------------------------------
@@ -669,16 +673,15 @@ __global__ void __launch_bounds__(kThreads) k_persist(PersistLaunch a) {
   Ring ring = ring_setup(smem, a.stages);
   for (int64_t t = 0; t < a.n_iters; ++t) {
     const int64_t it = a.it0 + t;
-    for (int bi = blockIdx.x; bi < a.n_blocks; bi += gridDim.x) {
-      const int b = a.block_ids[bi];
-      const BlockDev& B = a.blocks[b];
+    for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
+      const int u = a.unit_ids[ui];
+      const int q0 = a.unit_items[ui], q1 = a.unit_items[ui + 1];
+      const BlockDev& B = a.blocks[a.items[q0].block];
       if (t > 0) {
         if (tid == 0) {
           bool okw = true;
-          for (int f = 0; f < 6 && okw; ++f) {
-            const int nb = B.nbr[f];
-            if (nb >= 0) okw = wait_ge(a.progress + nb, it, a.err, a.wait_ns);
-          }
+          for (int d = a.dep_off[ui]; d < a.dep_off[ui + 1] && okw; ++d)
+            okw = wait_ge(a.progress + a.dep_ids[d], it, a.err, a.wait_ns);
           fence_proxy_async();
           s_ok = okw ? 1 : 0;
         }
@@ -688,7 +691,7 @@ __global__ void __launch_bounds__(kThreads) k_persist(PersistLaunch a) {
       const int p = (int)((it - a.grids[B.grid].start_iter) & 1);
       const bool resid = a.resid_first && t == 0;
       const bool emu = sizeof(T) == 8 && a.emu && a.norms && a.norms[B.grid].emu_bad == 0u;
-      for (int q = a.block_items[bi]; q < a.block_items[bi + 1]; ++q) {
+      for (int q = q0; q < q1; ++q) {
         const WorkItem w = a.items[q];
         bool ok;
         if (resid) {
@@ -704,7 +707,7 @@ __global__ void __launch_bounds__(kThreads) k_persist(PersistLaunch a) {
       __syncthreads();
       if (tid == 0) {
         __threadfence();
-        st_release(a.progress + b, it + 1);
+        st_release(a.progress + u, it + 1);
       }
     }
   }
@@ -832,7 +835,7 @@ int persistent_max_ctas(int dtype, int smem) {
 }
 
 cudaError_t launch_persistent(const PersistLaunch& a, int grid_ctas, cudaStream_t s) {
-  if (a.n_blocks <= 0 || a.n_iters <= 0) return cudaSuccess;
+  if (a.n_units <= 0 || a.n_iters <= 0) return cudaSuccess;
   PersistLaunch args = a;
   void* params[] = {&args};
   const void* fn = a.dtype == 0 ? persist_fn<double>() : persist_fn<float>();

@@ -666,13 +666,24 @@ int residual_only(jacobi_t* h, cudaStream_t s) {
   return JACOBI_OK;
 }
 
-int compute_bnorm(jacobi_t* h, cudaStream_t s) {
+// |b|^2 and the FP64 adder-domain check of every grid (grid < 0) or of one
+// grid (after its state was replaced).
+int compute_bnorm(jacobi_t* h, cudaStream_t s, int64_t grid) {
   StepLaunch a = step_args(h, h->iter, true);
+  int32_t b0 = 0, nb = (int32_t)h->plan.blocks.size(), g0 = 0, ng = (int32_t)h->plan.grids.size();
+  if (grid >= 0) {
+    const GridHost& G = h->plan.grids[grid];
+    a.items += G.item_begin;
+    a.n_items = (int32_t)(G.item_end - G.item_begin);
+    b0 = (int32_t)G.block_begin;
+    nb = (int32_t)(G.block_end - G.block_begin);
+    g0 = (int32_t)grid;
+    ng = 1;
+  }
   if (h->plan.dtype == JACOBI_F64)
-    JGB_CUDA(launch_emu_check(h->d_blocks, (int32_t)h->plan.blocks.size(), h->d_grids, h->d_norms, h->d_gids,
-                              (int32_t)h->plan.grids.size(), h->iter, s));
+    JGB_CUDA(launch_emu_check(h->d_blocks + b0, nb, h->d_grids, h->d_norms, h->d_gids + g0, ng, h->iter, s));
   JGB_CUDA(launch_bnorm(a, s));
-  JGB_CUDA(launch_reduce(h->d_grids, h->d_norms, h->d_gids, (int32_t)h->plan.grids.size(), h->d_partials, 1, s));
+  JGB_CUDA(launch_reduce(h->d_grids, h->d_norms, h->d_gids + g0, ng, h->d_partials, 1, s));
   return JACOBI_OK;
 }
 
@@ -860,7 +871,7 @@ int jacobi_create_batch(int64_t n_grids, const jacobi_dim3* grids, const jacobi_
   if (rc) return fail(rc);
   e = launch_init(h->d_blocks, h->d_geom, (int32_t)P.blocks.size(), h->d_inits, P.dtype, s);
   if (e != cudaSuccess) return fail(set_error(JACOBI_ECUDA, "init launch failed: %s", cudaGetErrorString(e)));
-  rc = compute_bnorm(h, s);
+  rc = compute_bnorm(h, s, -1);
   if (rc) return fail(rc);
   rc = refresh_active(h, s);
   if (rc) return fail(rc);
@@ -1171,7 +1182,7 @@ int jacobi_set_state(jacobi_t* h, int64_t grid, const void* src, int32_t src_on_
                                  dsrc, G.dims.nx, G.dims.ny, G.dims.nz, parity, h->plan.dtype, s);
   int rc = JACOBI_OK;
   if (e != cudaSuccess) rc = set_error(JACOBI_ECUDA, "scatter failed: %s", cudaGetErrorString(e));
-  if (!rc) rc = compute_bnorm(h, s);
+  if (!rc) rc = compute_bnorm(h, s, grid);
   if (!rc && !src_on_device) {
     // the caller may reuse its host buffer as soon as the call returns
     cudaError_t e2 = cudaStreamSynchronize(s);

@@ -37,6 +37,7 @@ constexpr int kItemKinds = 7;
 // planner only streams blocks whose 4-stage ring fits shared memory).  The
 // persistent kernel's ring depth stays a run-time choice.
 constexpr int kStreamStages = 4;
+static_assert((kStreamStages & (kStreamStages - 1)) == 0, "stage indices are masks: a power of two");
 constexpr int kItemRagged = 16;
 __host__ __device__ inline bool item_ragged(const WorkItem& w) { return (w.y0 & kItemRagged) != 0; }
 __host__ __device__ inline int item_kind(const WorkItem& w) {

@@ -616,30 +616,35 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, StreamShape<CW>::min
     const int tx = tid % txv, j0 = w.ya + (tid / txv) * RY;
     const bool active = j0 < w.yb;
     bool good = true;
+    // S is a power of two: stage = q & (S - 1), fill = q >> log2(S).  For FP64
+    // (S read at run time) this replaces four integer divisions per plane,
+    // a noticeable share of the integer pipe at 8 updates per thread and
+    // plane (same-box A/B: 512^3 140.8 -> 145.9 GLUP/s).
+    const int Sm = S - 1, Sl = 31 - __clz(S);
     for (int q = 1; q <= nplanes - 2 && good; ++q) {
       if (q == 1) {
         good = mbar_wait(full + 0, 0u, a.err, a.wait_ns) &&
-               mbar_wait(full + 1 % S, (uint32_t)(1 / S) & 1u, a.err, a.wait_ns);
+               mbar_wait(full + (1 & Sm), (uint32_t)(1 >> Sl) & 1u, a.err, a.wait_ns);
       }
       // FP32: inline test first (+1 to +1.5 % on small planes); FP64 keeps the
       // plain call, which ptxas allocates without extra spills.
       if (sizeof(T) == 4)
-        good = good && mbar_ready(full + (q + 1) % S, (uint32_t)((q + 1) / S) & 1u, a.err, a.wait_ns);
+        good = good && mbar_ready(full + ((q + 1) & Sm), (uint32_t)((q + 1) >> Sl) & 1u, a.err, a.wait_ns);
       else
-        good = good && mbar_wait(full + (q + 1) % S, (uint32_t)((q + 1) / S) & 1u, a.err, a.wait_ns);
+        good = good && mbar_wait(full + ((q + 1) & Sm), (uint32_t)((q + 1) >> Sl) & 1u, a.err, a.wait_ns);
       good = __all_sync(0xffffffffu, good);
       if (!good) break;
       if (active) {
-        const unsigned char* sm = stages + (size_t)((q - 1) % S) * L.bytes;
-        const unsigned char* sc = stages + (size_t)(q % S) * L.bytes;
-        const unsigned char* sp = stages + (size_t)((q + 1) % S) * L.bytes;
+        const unsigned char* sm = stages + (size_t)((q - 1) & Sm) * L.bytes;
+        const unsigned char* sc = stages + (size_t)(q & Sm) * L.bytes;
+        const unsigned char* sp = stages + (size_t)((q + 1) & Sm) * L.bytes;
         if (sizeof(T) == 8 && emu)
           acc += stream_plane<T, RY, MODE, true, RAG>(O, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
         else
           acc += stream_plane<T, RY, MODE, false, RAG>(O, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(empty + (q - 1) % S);
+      if (lane == 0) mbar_arrive(empty + ((q - 1) & Sm));
     }
   }
   if (MODE & kResid) {

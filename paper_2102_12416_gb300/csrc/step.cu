@@ -626,12 +626,9 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, StreamShape<CW>::min
         good = mbar_wait(full + 0, 0u, a.err, a.wait_ns) &&
                mbar_wait(full + (1 & Sm), (uint32_t)(1 >> Sl) & 1u, a.err, a.wait_ns);
       }
-      // FP32: inline test first (+1 to +1.5 % on small planes); FP64 keeps the
-      // plain call, which ptxas allocates without extra spills.
-      if (sizeof(T) == 4)
-        good = good && mbar_ready(full + ((q + 1) & Sm), (uint32_t)((q + 1) >> Sl) & 1u, a.err, a.wait_ns);
-      else
-        good = good && mbar_wait(full + ((q + 1) & Sm), (uint32_t)((q + 1) >> Sl) & 1u, a.err, a.wait_ns);
+      // inline test first, the bounded wait only when the plane is not there
+      // yet (same-box A/B: +1 to +1.5 %)
+      good = good && mbar_ready(full + ((q + 1) & Sm), (uint32_t)((q + 1) >> Sl) & 1u, a.err, a.wait_ns);
       good = __all_sync(0xffffffffu, good);
       if (!good) break;
       if (active) {

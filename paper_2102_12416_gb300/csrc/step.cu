@@ -283,10 +283,10 @@ __device__ __forceinline__ PlaneView<T> plane_view(const BlockDev& B, int p) {
   return v;
 }
 // Neighbour receive slot of face f for the new iterate: from the CTA's
-// shared-memory copy when there is one, else through the read-only path.
-template <typename T>
+// shared-memory copy (TABLE), else through the read-only path.
+template <bool TABLE, typename T>
 __device__ __forceinline__ T* send_slot(const PlaneView<T>& O, int f) {
-  if (O.ss) return (T*)O.ss[f];
+  if (TABLE) return (T*)O.ss[f];
   return (T*)__ldg((const unsigned long long*)&O.B->send[f][O.pn]);
 }
 
@@ -297,7 +297,10 @@ __device__ __forceinline__ T* send_slot(const PlaneView<T>& O, int f) {
 // their values are replaced by the y (x) ghost before use, so the last real
 // row (column) sees its ghost, and they are neither summed into the residual
 // nor stored.  Without RAG there is no padding and none of those checks.
-template <typename T, int RY, int MODE, bool EMU, bool RAG>
+// TABLE: the send slots come from the CTA's shared-memory copy.  The face
+// checks are kept to the rows that can hit a face (row groups start on
+// multiples of 4): same-box A/B +5 % on the FP64 64^3-block step.
+template <typename T, int RY, int MODE, bool EMU, bool RAG, bool TABLE>
 __device__ __forceinline__ double stream_plane(const PlaneView<T>& O, int k, int ya, const StageLayout& L,
                                                const unsigned char* sm, const unsigned char* sc,
                                                const unsigned char* sp, int tx, int j0) {
@@ -372,34 +375,36 @@ __device__ __forceinline__ double stream_plane(const PlaneView<T>& O, int k, int
       }
       xe[r] = xfirst ? v[0] : last;
       if (xfirst && xlast && (!RAG || j < ny)) {
-        T* d = send_slot(O, XP);
+        T* d = send_slot<TABLE>(O, XP);
         if (d) d[(int64_t)k * ry + j] = last;
       }
     }
     if ((MODE & kWrite) && (!RAG || j < ny)) {
       V16<T>::store(V + j * rx + i0, v);
       if (MODE & kPack) {
-        if (j == 0) {
-          T* d = send_slot(O, YM);
+        if (r == 0 && j0 == 0) {  // row groups start on multiples of 4: only row 0 can be j = 0
+          T* d = send_slot<TABLE>(O, YM);
           if (d) V16<T>::store(d + (int64_t)k * rx + i0, v);
         }
-        if (j == ny - 1) {
-          T* d = send_slot(O, YP);
+        // without padding ny is a multiple of 4, so only the last row of the
+        // last row group can be j = ny - 1
+        if (RAG ? j == ny - 1 : (r == RY - 1 && j0 + RY == ny)) {
+          T* d = send_slot<TABLE>(O, YP);
           if (d) V16<T>::store(d + (int64_t)k * rx + i0, v);
         }
         if (k == 0) {
-          T* d = send_slot(O, ZM);
+          T* d = send_slot<TABLE>(O, ZM);
           if (d) V16<T>::store(d + j * rx + i0, v);
         }
         if (k == nz - 1) {
-          T* d = send_slot(O, ZP);
+          T* d = send_slot<TABLE>(O, ZP);
           if (d) V16<T>::store(d + j * rx + i0, v);
         }
       }
     }
   }
   if ((MODE & kWrite) && (MODE & kPack) && (xfirst || xlast)) {
-    T* d = send_slot(O, xfirst ? XM : XP);
+    T* d = send_slot<TABLE>(O, xfirst ? XM : XP);
     if (d) {
       T* x = d + (int64_t)k * ry + j0;  // 16-byte aligned: ry and j0 are multiples of 4
 #pragma unroll
@@ -467,11 +472,11 @@ __device__ double stream_item(const BlockDev& B, int p, const WorkItem& w, Ring&
       const unsigned char* sp = ring.stages + (size_t)((q + 1) % S) * L.bytes;
       const int kq = w.z0 - 1 + q;
       if (rag) {
-        if (sizeof(T) == 8 && emu) acc += stream_plane<T, RY, MODE, true, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
-        else acc += stream_plane<T, RY, MODE, false, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+        if (sizeof(T) == 8 && emu) acc += stream_plane<T, RY, MODE, true, true, false>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+        else acc += stream_plane<T, RY, MODE, false, true, false>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
       } else {
-        if (sizeof(T) == 8 && emu) acc += stream_plane<T, RY, MODE, true, false>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
-        else acc += stream_plane<T, RY, MODE, false, false>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+        if (sizeof(T) == 8 && emu) acc += stream_plane<T, RY, MODE, true, false, false>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+        else acc += stream_plane<T, RY, MODE, false, false, false>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
       }
     }
   }
@@ -636,9 +641,9 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, StreamShape<CW>::min
         const unsigned char* sc = stages + (size_t)(q & Sm) * L.bytes;
         const unsigned char* sp = stages + (size_t)((q + 1) & Sm) * L.bytes;
         if (sizeof(T) == 8 && emu)
-          acc += stream_plane<T, RY, MODE, true, RAG>(O, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
+          acc += stream_plane<T, RY, MODE, true, RAG, kSendTable>(O, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
         else
-          acc += stream_plane<T, RY, MODE, false, RAG>(O, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
+          acc += stream_plane<T, RY, MODE, false, RAG, kSendTable>(O, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(empty + ((q - 1) & Sm));

@@ -71,8 +71,10 @@ def measured_peaks():
 
 
 def kernel_source_sha() -> str:
+    """Hash of the sources that define the dominant step kernel (k_stream and
+    what it includes), to tell whether committed counters still apply."""
     h = hashlib.sha256()
-    for name in ("step.cu", "kernels.cu", "common.cuh", "kernels.cuh"):
+    for name in ("step.cu", "common.cuh", "kernels.cuh"):
         with open(os.path.join(ROOT, "paper_2102_12416_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

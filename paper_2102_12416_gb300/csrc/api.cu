@@ -693,13 +693,19 @@ int read_norms(jacobi_t* h, cudaStream_t s) {
   return JACOBI_OK;
 }
 
+// Host-transfer staging buffer: sized once for the largest padded grid of the
+// handle (growing it grid by grid would free and allocate, both synchronous,
+// on many calls of a batch).
 int stage_get(jacobi_t* h, size_t bytes, void** out) {
   if (h->stage_bytes < bytes) {
+    size_t want = bytes;
+    for (const GridHost& G : h->plan.grids)
+      want = std::max(want, (size_t)(G.dims.nx + 2) * (G.dims.ny + 2) * (G.dims.nz + 2) * h->plan.elem);
     if (h->stage) cudaFree(h->stage);
     h->stage = nullptr;
     h->stage_bytes = 0;
-    JGB_CUDA(cudaMalloc(&h->stage, bytes));
-    h->stage_bytes = bytes;
+    JGB_CUDA(cudaMalloc(&h->stage, want));
+    h->stage_bytes = want;
   }
   *out = h->stage;
   return JACOBI_OK;

@@ -73,6 +73,18 @@ __device__ __forceinline__ int64_t cell(const BlockDev& B, int64_t i, int64_t j,
   return k * B.plane_pitch + j * B.rx + i;
 }
 
+// Calls f(i, j, k) for every interior point of B: the CTA's warps take the
+// rows (j, k) in turn, the lanes walk a row (coalesced; one division per row).
+template <typename F>
+__device__ __forceinline__ void for_interior(const BlockDev& B, F f) {
+  const int nx = B.nx, ny = B.ny, rows = B.ny * B.nz;
+  const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int row = threadIdx.x >> 5; row < rows; row += nwarps) {
+    const int k = row / ny, j = row - k * ny;
+    for (int i = lane; i < nx; i += 32) f(i, j, k);
+  }
+}
+
 template <typename T>
 __global__ void k_init_interior(const BlockDev* __restrict__ blocks, const BlockGeom* __restrict__ geom,
                                 const InitDev* __restrict__ inits) {
@@ -80,10 +92,12 @@ __global__ void k_init_interior(const BlockDev* __restrict__ blocks, const Block
   const BlockGeom G = geom[blockIdx.x];
   const InitDev I = inits[G.grid];
   T* U = (T*)B.u[0];
-  const int64_t nx = B.nx, ny = B.ny, n = nx * ny * B.nz;
+  // a flat walk: for a zero interior this is a pure store stream, which the
+  // row-wise walk issued ~3x slower
+  const int64_t nx = B.nx, ny = B.ny, n = nx * ny * B.nz, pitch = B.plane_pitch, rx = B.rx;
   for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
     const int64_t i = e % nx, j = (e / nx) % ny, k = e / (nx * ny);
-    U[cell(B, i, j, k)] = to_state<T>(init_value(I, G.ox + 1 + i, G.oy + 1 + j, G.oz + 1 + k));
+    U[k * pitch + j * rx + i] = to_state<T>(init_value(I, G.ox + 1 + i, G.oy + 1 + j, G.oz + 1 + k));
   }
 }
 
@@ -111,11 +125,10 @@ __global__ void k_scatter(const BlockDev* __restrict__ blocks, const BlockGeom* 
   const int64_t px = NX + 2, py = NY + 2;
   if (blockIdx.y == 0) {
     T* U = (T*)B.u[parity];
-    const int64_t nx = B.nx, ny = B.ny, n = nx * ny * B.nz;
-    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
-      const int64_t i = e % nx, j = (e / nx) % ny, k = e / (nx * ny);
-      U[cell(B, i, j, k)] = src[((G.oz + 1 + k) * py + (G.oy + 1 + j)) * px + (G.ox + 1 + i)];
-    }
+    const int64_t pitch = B.plane_pitch, rx = B.rx;
+    for_interior(B, [=](int i, int j, int k) {
+      U[k * pitch + j * rx + i] = src[((G.oz + 1 + k) * py + (G.oy + 1 + j)) * px + (G.ox + 1 + i)];
+    });
   } else {
     const int f = blockIdx.y - 1;
     T* S = (T*)B.recv[f][parity];
@@ -137,12 +150,10 @@ __global__ void k_gather(const BlockDev* __restrict__ blocks, const BlockGeom* _
   const int64_t px = NX + 2 * off, py = NY + 2 * off;
   if (blockIdx.y == 0) {
     const T* U = (const T*)B.u[parity];
-    const int64_t nx = B.nx, ny = B.ny, n = nx * ny * B.nz;
-    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
-      const int64_t i = e % nx, j = (e / nx) % ny, k = e / (nx * ny);
-      dst[((G.oz + off + k) * py + (G.oy + off + j)) * px + (G.ox + off + i)] =
-          U[cell(B, i, j, k)];
-    }
+    const int64_t pitch = B.plane_pitch, rx = B.rx;
+    for_interior(B, [=](int i, int j, int k) {
+      dst[((G.oz + off + k) * py + (G.oy + off + j)) * px + (G.ox + off + i)] = U[k * pitch + j * rx + i];
+    });
   } else if (padded) {
     const int f = blockIdx.y - 1;
     if (B.nbr[f] >= 0) return;  // only Dirichlet faces lie on the padded boundary
@@ -200,9 +211,8 @@ __global__ void k_emu_check(const BlockDev* __restrict__ blocks, const GridDev* 
   const int p = (int)((it - grids[B.grid].start_iter) & 1);
   const uint32_t* U = (const uint32_t*)B.u[p];
   bool bad = false;
-  const int64_t nx = B.nx, ny = B.ny, n = nx * ny * B.nz;
-  for (int64_t e = threadIdx.x; e < n; e += blockDim.x)
-    bad |= U[2 * cell(B, e % nx, (e / nx) % ny, e / (nx * ny)) + 1] >= kEmuHiLimit;
+  const int64_t pitch = B.plane_pitch, rx = B.rx;
+  for_interior(B, [&](int i, int j, int k) { bad |= U[2 * (k * pitch + j * rx + i) + 1] >= kEmuHiLimit; });
   for (int f = 0; f < 6; ++f) {
     const uint32_t* S = (const uint32_t*)B.recv[f][p];
     const int64_t m = face_elems(B, f);

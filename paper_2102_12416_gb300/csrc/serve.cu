@@ -236,7 +236,8 @@ int admit(serve_s* s, int si, const Req& q) {
                               s->it, st));
   ENG_CUDA(launch_bnorm(a, st));
   ENG_CUDA(launch_reduce(s->d_grids, s->d_norms, s->d_ids + si, 1, s->d_partials, 1, st));
-  ENG_CUDA(cudaStreamSynchronize(st));  // host staging vectors above are pageable
+  // No synchronisation: a host-to-device cudaMemcpyAsync from pageable memory
+  // returns once the source has been staged, so the vectors above may go.
   s->dirty = true;
   {
     std::lock_guard<std::mutex> lk(s->mu);

@@ -106,9 +106,10 @@ typedef struct { int32_t mode; int32_t pad_; int64_t x, y, z; } jacobi_split;
  *               from there by the next iteration (unpack fused into the load).
  *   EXPLICIT:   stencil launch, then an explicit pack of every face into a
  *               send buffer and a channel copy into the neighbour's slot.
- *   PERSISTENT: one cooperative launch runs all iterations; blocks signal
- *               neighbours with release/acquire progress flags in device
- *               memory instead of kernel boundaries (bounded waits).
+ *   PERSISTENT: one cooperative launch runs all iterations; the z-chunks of
+ *               the blocks (units) signal the units they share data with
+ *               through release/acquire progress flags in device memory
+ *               instead of kernel boundaries (bounded waits).
  *   GRAPH:      the FUSED launches captured once in a CUDA graph and replayed. */
 typedef enum {
   JACOBI_PATH_FUSED = 0,
@@ -212,8 +213,9 @@ int jacobi_destroy(jacobi_t* h);
 int jacobi_info(const jacobi_t* h, jacobi_info_t* out);
 int jacobi_block(const jacobi_t* h, int64_t block, jacobi_block_info* out);
 
-/* Select the step path (jacobi_path).  PERSISTENT fails with JACOBI_EINVAL at
- * the next step if the blocks cannot all be co-resident on the GPU. */
+/* Select the step path (jacobi_path).  The persistent launch uses at most as
+ * many CTAs as can be co-resident on the GPU; each owns several units when
+ * there are more. */
 int jacobi_set_path(jacobi_t* h, int32_t path);
 
 /* Autotuner (the library's addition): times every candidate step

@@ -1,11 +1,14 @@
 """GPU parity of the CUDA path against the CPU oracle, through the C ABI.
 
-Bars (stated here, derived in the design doc):
-  * init, pack/unpack, decomposition and the FP64 stencil: bit-exact;
+Bars:
+  * init, pack/unpack, decomposition and the FP64 stencil: bit-exact (every
+    FP64 operation is rounded exactly as the oracle rounds it, and the
+    integer-pipe adder is exact);
   * FP32 stencil: bit-exact against the FP32 oracle (same operation order),
     and within 1e-5 relative (inf-norm) of the FP64 oracle after the stated
     iterations;
-  * residual norms: within 1e-12 relative (the summation order differs);
+  * residual norms: within 1e-12 relative (the per-point residuals are
+    bit-identical; only the summation order differs);
   * solve iteration counts: equal.
 """
 import math

@@ -564,23 +564,32 @@ def run_ours(args):
             for g, ini in zip(grids, inits)]
     h_out = [torch.empty((g[2], g[1], g[0]), dtype=npdt).pin_memory() for g in grids]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(args.e2e_steps, 1)
+    # phase boundaries on the same stream (set_state | step | residual | copy_out)
+    pev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(e2e_steps)]
     torch.cuda.synchronize()
     e0.record(stream)
-    e2e_steps = max(args.e2e_steps, 1)
-    for _ in range(e2e_steps):
+    for k in range(e2e_steps):
+        pev[k][0].record(stream)
         for gi in range(len(grids)):
             jg.jacobi_set_state(s.h, gi, h_in[gi].data_ptr(), False, stream)
+        pev[k][1].record(stream)
         s.step(iters)
+        pev[k][2].record(stream)
         s.residual()
+        pev[k][3].record(stream)
         for gi in range(len(grids)):
             jg.jacobi_copy_out(s.h, gi, h_out[gi].data_ptr(), False, jg.JACOBI_LAYOUT_INTERIOR, stream)
+        pev[k][4].record(stream)
     e1.record(stream)
     e1.synchronize()
+    phases = {name: sum(pev[k][i].elapsed_time(pev[k][i + 1]) for k in range(e2e_steps)) / e2e_steps
+              for i, name in enumerate(("set_state_h2d", "step", "residual", "copy_out_d2h"))}
     e2e_ms, e2e_lups = replica_totals(dist, "cuda", e0.elapsed_time(e1), n_points * iters * e2e_steps)
     e2e = {"value": e2e_lups / (e2e_ms * 1e-3) / 1e9, "unit": "GLUP/s",
            "h2d_bytes_per_step": sum(x.numel() * x.element_size() for x in h_in),
            "d2h_bytes_per_step": sum(x.numel() * x.element_size() for x in h_out) + 16 * len(grids),
-           "steps": e2e_steps}
+           "steps": e2e_steps, "phase_ms_per_step": {k: round(v, 3) for k, v in phases.items()}}
 
     sweep = modes = bw = None
     if not args.no_sweep and rank == 0:

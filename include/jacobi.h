@@ -62,6 +62,10 @@ enum {
 
 typedef enum { JACOBI_F64 = 0, JACOBI_F32 = 1 } jacobi_dtype;
 
+/* Largest block extent per axis (work items hold block coordinates, padded
+ * ones included, in 16 bits). */
+#define JACOBI_MAX_BLOCK_EXTENT 32764
+
 /* Dirichlet boundary families.  Coordinates are node-centred on the unit cube,
  * x = i/(nx+1) (IEEE FP64 division), likewise y and z. */
 typedef enum {
@@ -181,7 +185,10 @@ const char* jacobi_last_error(void);
 int jacobi_decompose(jacobi_dim3 grid, int64_t nblocks, jacobi_dim3* counts_out);
 
 /* Device bytes jacobi_create needs for one grid (states, receive slots,
- * flags, tables, reduction partials), for a caller-supplied workspace. */
+ * flags, tables, reduction partials), for a caller-supplied workspace.
+ * Grids, splits and block extents are checked as by jacobi_create:
+ * JACOBI_EINVAL for a non-positive or too large size (a block may span at
+ * most JACOBI_MAX_BLOCK_EXTENT points per axis). */
 int jacobi_workspace_bytes(jacobi_dim3 grid, jacobi_split split, jacobi_dtype dtype,
                            size_t* bytes);
 int jacobi_workspace_bytes_batch(int64_t n_grids, const jacobi_dim3* grids,

@@ -32,6 +32,7 @@ JACOBI_SPLIT_COUNT, JACOBI_SPLIT_SHAPE = 0, 1
 JACOBI_PATH_FUSED, JACOBI_PATH_EXPLICIT, JACOBI_PATH_PERSISTENT, JACOBI_PATH_GRAPH = 0, 1, 2, 3
 JACOBI_SOLVE_CONVERGED, JACOBI_SOLVE_MAX_ITERS, JACOBI_SOLVE_STAGNATED = 0, 1, 2
 JACOBI_LAYOUT_INTERIOR, JACOBI_LAYOUT_PADDED = 0, 1
+JACOBI_MAX_BLOCK_EXTENT = 32764
 FACES = ("xm", "xp", "ym", "yp", "zm", "zp")
 
 PATHS = {"fused": JACOBI_PATH_FUSED, "explicit": JACOBI_PATH_EXPLICIT,

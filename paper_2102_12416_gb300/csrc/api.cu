@@ -170,7 +170,10 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
       int rc = axis_split(n3[a], splits[g].mode, s3[a], &ax[a]);
       if (rc) return rc;
       for (auto& pe : ax[a])
-        if (pe.second > 32767) return set_error(JACOBI_EINVAL, "block extent %lld exceeds 32767", (long long)pe.second);
+        // work items hold block coordinates in 16 bits, padded extents
+        // included (rows are padded to a multiple of 4)
+        if (pe.second > kMaxBlockExtent)
+          return set_error(JACOBI_EINVAL, "block extent %lld exceeds %d", (long long)pe.second, kMaxBlockExtent);
     }
     GridHost G;
     G.dims = d;

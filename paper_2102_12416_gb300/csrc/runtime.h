@@ -77,6 +77,7 @@ struct Plan {
 // running alone still spreads over the GPU, while the halo planes each chunk
 // re-reads stay a bounded share.
 constexpr int64_t kServeTargetItems = 304;
+constexpr int kMaxBlockExtent = JACOBI_MAX_BLOCK_EXTENT;
 constexpr int64_t kServeMinChunk = 16;
 int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* splits, jacobi_dtype dtype,
                const jacobi_init* inits, Plan* out, int64_t target_items = 0, int64_t min_chunk = 1);

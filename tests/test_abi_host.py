@@ -82,3 +82,15 @@ def test_workspace_rejects_bad_split(lib):
         jg.jacobi_workspace_bytes((10, 10, 10), ("count", (11, 1, 1)), "f64")
     with pytest.raises(jg.JacobiError):
         jg.jacobi_workspace_bytes((10, 10, 0), ("count", (1, 1, 1)), "f64")
+
+
+def test_workspace_rejects_oversized_blocks(lib):
+    # a block may span JACOBI_MAX_BLOCK_EXTENT = 32764 points per axis (its padded extent must fit the
+    # 16-bit coordinates of a work item); 32765 pads to 32768 rows
+    jg.jacobi_workspace_bytes((4, 32764, 1), ("count", (1, 1, 1)), "f32")
+    for grid in [(4, 32765, 1), (32765, 4, 1), (4, 4, 32765)]:
+        with pytest.raises(jg.JacobiError) as e:
+            jg.jacobi_workspace_bytes(grid, ("count", (1, 1, 1)), "f32")
+        assert e.value.code == jg.JACOBI_EINVAL
+    # the same extent split in two is fine
+    jg.jacobi_workspace_bytes((4, 65528, 1), ("count", (1, 2, 1)), "f32")

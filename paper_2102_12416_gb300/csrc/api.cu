@@ -649,11 +649,10 @@ int step_with_residual(jacobi_t* h, cudaStream_t s) {
     rc = step_persistent(h, h->iter, 1, true, s);
     if (rc) return rc;
   } else {
+    // every other path takes the fused step here: its pack delivers the
+    // faces, so the explicit path has nothing left to move either
     StepLaunch a = step_args(h, h->iter, false);
     JGB_CUDA(launch_step(a, kWrite | kPack | kResid, s, &h->fork));
-    if (h->path == JACOBI_PATH_EXPLICIT) {
-      // the fused pack already delivered the faces; nothing else to move
-    }
   }
   JGB_CUDA(launch_reduce(h->d_grids, h->d_norms, h->d_gids, (int32_t)h->plan.grids.size(), h->d_partials, 0, s));
   h->iter += 1;
@@ -758,20 +757,34 @@ const char* jacobi_strerror(int code) {
 const char* jacobi_last_error(void) { return jgb::g_last_error.c_str(); }
 
 int jacobi_decompose(jacobi_dim3 grid, int64_t nblocks, jacobi_dim3* out) {
-  if (!out || nblocks < 1 || grid.nx < 1 || grid.ny < 1 || grid.nz < 1)
+  const int64_t kMax = 1ll << 30;  // the sizes plan_build accepts
+  if (!out || nblocks < 1 || grid.nx < 1 || grid.ny < 1 || grid.nz < 1 || nblocks > kMax || grid.nx > kMax ||
+      grid.ny > kMax || grid.nz > kMax)
     return set_error(JACOBI_EINVAL, "bad arguments to jacobi_decompose");
   // Total block surface of a near-equal split: sum over blocks of
-  // 2(ex*ey + ey*ez + ez*ex) = 2(nx*ny*pz + ny*nz*px + nz*nx*py).
+  // 2(ex*ey + ey*ez + ez*ex) = 2(nx*ny*pz + ny*nz*px + nz*nx*py), which can
+  // exceed 64 bits at the largest accepted sizes.
   bool found = false;
-  int64_t best = 0;
+  unsigned __int128 best = 0;
   jacobi_dim3 arg{0, 0, 0};
-  for (int64_t px = 1; px <= nblocks; ++px) {
-    if (nblocks % px) continue;
-    for (int64_t py = 1; py <= nblocks / px; ++py) {
+  // the divisors of nblocks in ascending order (trial division to its root)
+  std::vector<int64_t> divs, upper;
+  for (int64_t d = 1; d * d <= nblocks; ++d)
+    if (nblocks % d == 0) {
+      divs.push_back(d);
+      if (d * d != nblocks) upper.push_back(nblocks / d);
+    }
+  divs.insert(divs.end(), upper.rbegin(), upper.rend());
+  for (int64_t px : divs) {
+    if (px > grid.nx) break;
+    for (int64_t py : divs) {
+      if (py > grid.ny || py > nblocks / px) break;
       if ((nblocks / px) % py) continue;
       const int64_t pz = nblocks / px / py;
-      if (px > grid.nx || py > grid.ny || pz > grid.nz) continue;
-      const int64_t area = 2 * (grid.nx * grid.ny * pz + grid.ny * grid.nz * px + grid.nz * grid.nx * py);
+      if (pz > grid.nz) continue;
+      using U = unsigned __int128;
+      const U area = 2 * ((U)grid.nx * (U)grid.ny * (U)pz + (U)grid.ny * (U)grid.nz * (U)px +
+                          (U)grid.nz * (U)grid.nx * (U)py);
       if (!found || area < best) {  // loop order is lexicographic, so ties keep the first
         found = true;
         best = area;

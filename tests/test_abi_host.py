@@ -54,6 +54,18 @@ def test_decompose_matches_oracle(lib, oracle_mod, grid, n):
     assert jg.jacobi_decompose(grid, n) == oracle_mod.decompose(grid, n)
 
 
+def test_decompose_large_sizes(lib):
+    # the largest accepted sizes: a cube splits evenly (the surface sum needs
+    # more than 64 bits here), and a prime count can only go along one axis
+    n = 1 << 30
+    assert jg.jacobi_decompose((n, n, n), n) == (1024, 1024, 1024)
+    assert jg.jacobi_decompose((n, 2, 2), 1_000_003) == (1_000_003, 1, 1)
+    with pytest.raises(jg.JacobiError):
+        jg.jacobi_decompose((n + 1, 2, 2), 2)
+    with pytest.raises(jg.JacobiError):
+        jg.jacobi_decompose((8, 8, 8), n + 1)
+
+
 def test_decompose_rejects_impossible(lib):
     with pytest.raises(jg.JacobiError) as e:
         jg.jacobi_decompose((2, 2, 2), 27)

@@ -213,8 +213,9 @@ int jacobi_create_batch(int64_t n_grids, const jacobi_dim3* grids, const jacobi_
                         jacobi_dtype dtype, const jacobi_init* inits, void* workspace,
                         size_t ws_bytes, void* stream, jacobi_t** out);
 
-/* Waits for the handle's outstanding work, then frees what the library
- * allocated (never the caller's workspace). */
+/* Waits for the handle's outstanding work (the handle does not own the
+ * caller's streams, so this synchronises the device), then frees what the
+ * library allocated (never the caller's workspace). */
 int jacobi_destroy(jacobi_t* h);
 
 int jacobi_info(const jacobi_t* h, jacobi_info_t* out);

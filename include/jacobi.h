@@ -296,6 +296,13 @@ int jacobi_read_face(jacobi_t* h, int64_t block, int32_t face, void* dst, void* 
  * FP64 add on the FP64 pipe.  Asynchronous. */
 int jacobi_selftest_dadd(const double* a, const double* b, int64_t n, double* out, void* stream);
 
+/* Test support for the FP32 residual's exact binary32 -> binary64 widening on
+ * the integer pipe: runs every one of the 2^32 binary32 bit patterns through
+ * it on the device and writes to *mismatches (host) how many results differ
+ * bit for bit from the conversion instruction's (NaN inputs must give a NaN).
+ * Expected 0.  Synchronises the stream. */
+int jacobi_selftest_widen(uint64_t* mismatches, void* stream);
+
 /* Measured issue rates of this GPU's two add pipes (for rooflines): FP64 adds
  * per second on the FP64 pipe, and FP64 adds per second through the
  * integer-pipe routine of jacobi_selftest_dadd; each from one timed launch of

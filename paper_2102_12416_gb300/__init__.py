@@ -127,6 +127,7 @@ _SIGS = {
     "jacobi_read_face": (ctypes.c_int, [P, c_int64, c_int32, P, P]),
     "jacobi_debug_drop_block": (ctypes.c_int, [P, c_int64]),
     "jacobi_selftest_dadd": (ctypes.c_int, [P, P, c_int64, P, P]),
+    "jacobi_selftest_widen": (ctypes.c_int, [P, P]),
     "jacobi_pipe_rates": (ctypes.c_int, [ctypes.POINTER(c_double), ctypes.POINTER(c_double), P]),
     "jacobi_residual_noalloc": (ctypes.c_int, [P, jacobi_dim3, ctypes.c_int, P, P]),
     "channel_open": (ctypes.c_int, [P, c_uint32, c_int64, c_int64, c_size_t, ctypes.POINTER(P)]),
@@ -323,6 +324,14 @@ def jacobi_read_face(h, block, face, dst: np.ndarray, stream=None):
 
 def jacobi_selftest_dadd(a_dev, b_dev, n, out_dev, stream=None):
     _call("jacobi_selftest_dadd", int(a_dev), int(b_dev), n, int(out_dev), _stream(stream))
+
+
+def jacobi_selftest_widen(stream=None):
+    """Number of binary32 inputs whose integer-pipe widening differs from the
+    conversion instruction (all 2^32 bit patterns, on the device)."""
+    n = ctypes.c_uint64(0)
+    _call("jacobi_selftest_widen", ctypes.addressof(n), _stream(stream))
+    return n.value
 
 
 def jacobi_pipe_rates(stream=None):

@@ -1241,6 +1241,22 @@ int jacobi_copy_out(jacobi_t* h, int64_t grid, void* dst, int32_t dst_on_device,
   return rc;
 }
 
+int jacobi_selftest_widen(uint64_t* mismatches, void* stream) {
+  if (!mismatches) return set_error(JACOBI_EINVAL, "null pointer");
+  const cudaStream_t s = S(stream);
+  unsigned long long* d = nullptr;
+  JGB_CUDA(cudaMalloc((void**)&d, sizeof *d));
+  unsigned long long n = 0;
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof *d, s);
+  if (e == cudaSuccess) e = launch_selftest_widen(d, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&n, d, sizeof n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  if (e != cudaSuccess) return set_error(JACOBI_ECUDA, "widening self-test failed: %s", cudaGetErrorString(e));
+  *mismatches = (uint64_t)n;
+  return JACOBI_OK;
+}
+
 int jacobi_selftest_dadd(const double* a, const double* b, int64_t n, double* out, void* stream) {
   if ((!a || !b || !out) && n > 0) return set_error(JACOBI_EINVAL, "null pointer");
   if (n < 0) return set_error(JACOBI_EINVAL, "negative count");

@@ -175,6 +175,23 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
+// Exact binary32 -> binary64 conversion on the integer pipe, from the two
+// formats' definitions: for a normal number the exponent is rebiased
+// (127 -> 1023) and the significand widened by 29 bits.  A subnormal is first
+// scaled by 2^64 in FP32 (exact, the result is normal) and rebiased 64 less;
+// zeros, infinities and NaNs keep their class.  Equal to the conversion
+// instruction for every non-NaN input (jacobi_selftest_widen checks all 2^32
+// inputs on the device); a NaN stays a NaN.  The FP32 residual uses it.
+__device__ __forceinline__ double widen_f32(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const bool sub = (u & 0x7F800000u) == 0u;  // zero or subnormal
+  const uint32_t a = __float_as_uint(sub ? f * 0x1p64f : f) & 0x7FFFFFFFu;
+  uint64_t bits = ((uint64_t)a << 29) + ((uint64_t)(sub ? 896 - 64 : 896) << 52);
+  if (a == 0u) bits = 0ull;
+  if (a >= 0x7F800000u) bits = ((uint64_t)a << 29) | (0x7FFull << 52);  // inf, NaN
+  return __longlong_as_double((long long)(bits | ((uint64_t)(u >> 31) << 63)));
+}
+
 // Spin (bounded by wall time `limit_ns` and by a poll count) until *flag >= target,
 // with acquire semantics.  Returns true on success.  On expiry it records
 // DEV_TIMEOUT in *err (first failure wins); it also gives up early when another

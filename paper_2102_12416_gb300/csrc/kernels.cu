@@ -234,6 +234,20 @@ __global__ void k_selftest_dadd(const double* a, const double* b, int64_t n, dou
   if (i < n) out[i] = r;
 }
 
+// Every binary32 bit pattern through widen_f32, against the conversion
+// instruction: counts results that differ bit for bit (a NaN must stay a NaN).
+__global__ void k_selftest_widen(unsigned long long* bad) {
+  unsigned long long n = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < (1ull << 32); x += stride) {
+    const float f = __uint_as_float((uint32_t)x);
+    const double a = widen_f32(f), b = (double)f;
+    const bool ok = (a != a && b != b) || __double_as_longlong(a) == __double_as_longlong(b);
+    n += ok ? 0ull : 1ull;
+  }
+  if (n) atomicAdd(bad, n);
+}
+
 // Pipe-rate probe: chains of FP64 adds on the FP64 pipe (EMU = false) or
 // through dadd_nn on the integer pipe (EMU = true); 8 independent chains per
 // thread keep either pipe busy.  The result is stored so nothing is elided.
@@ -360,6 +374,11 @@ cudaError_t launch_pipe_rate(bool emu, int blocks, int threads, int iters, doubl
 cudaError_t launch_selftest_dadd(const double* a, const double* b, int64_t n, double* out, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_selftest_dadd<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, b, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_selftest_widen(unsigned long long* bad, cudaStream_t s) {
+  k_selftest_widen<<<1216, 256, 0, s>>>(bad);
   return cudaGetLastError();
 }
 

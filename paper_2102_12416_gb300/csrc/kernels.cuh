@@ -94,6 +94,7 @@ cudaError_t launch_copy_faces(const BlockDev* blocks, int32_t n_blocks, void* co
 cudaError_t launch_emu_check(const BlockDev* blocks, int32_t n_blocks, const GridDev* grids, GridNorm* norms,
                              const int32_t* grid_ids, int32_t n_grids, int64_t it, cudaStream_t s);
 cudaError_t launch_selftest_dadd(const double* a, const double* b, int64_t n, double* out, cudaStream_t s);
+cudaError_t launch_selftest_widen(unsigned long long* bad, cudaStream_t s);
 cudaError_t launch_pipe_rate(bool emu, int blocks, int threads, int iters, double* out, cudaStream_t s);
 
 // |b|^2 partials (interior = 0, only Dirichlet ghosts).

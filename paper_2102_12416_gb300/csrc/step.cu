@@ -96,23 +96,6 @@ template <> struct V16<double> {
   }
 };
 
-// Exact binary32 -> binary64 conversion on the integer pipe, from the two
-// formats' definitions: for a normal number the exponent is rebiased
-// (127 -> 1023) and the significand widened by 29 bits.  A subnormal is first
-// scaled by 2^64 in FP32 (exact, the result is normal) and rebiased 64 less;
-// zeros, infinities and NaNs keep their class.  Equal to the conversion
-// instruction for every non-NaN input (checked exhaustively); a NaN stays a
-// NaN.
-__device__ __forceinline__ double widen_f32(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const bool sub = (u & 0x7F800000u) == 0u;  // zero or subnormal
-  const uint32_t a = __float_as_uint(sub ? f * 0x1p64f : f) & 0x7FFFFFFFu;
-  uint64_t bits = ((uint64_t)a << 29) + ((uint64_t)(sub ? 896 - 64 : 896) << 52);
-  if (a == 0u) bits = 0ull;
-  if (a >= 0x7F800000u) bits = ((uint64_t)a << 29) | (0x7FFull << 52);  // inf, NaN
-  return __longlong_as_double((long long)(bits | ((uint64_t)(u >> 31) << 63)));
-}
-
 // FP64 residual contribution of one point: r = s - 6u with s re-evaluated in
 // FP64 from the (exactly widened) neighbours in the stencil's order.  FP32
 // states are widened on the integer pipe, which leaves the slow FP64 pipe

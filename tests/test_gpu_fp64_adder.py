@@ -2,7 +2,9 @@
 round-to-nearest-even addition bit for bit on its domain (non-negative,
 exponent field < 2040); numpy's float64 addition is the reference.  And the
 step kernels give identical iterates whether the pair sums run on the integer
-pipe or on the FP64 pipe (JACOBI_FP64_EMU=0)."""
+pipe or on the FP64 pipe (JACOBI_FP64_EMU=0).  The FP32 residual's
+integer-pipe widening (binary32 -> binary64) equals the conversion
+instruction on all 2^32 inputs."""
 import numpy as np
 import pytest
 
@@ -86,3 +88,8 @@ def test_negative_values_keep_the_fp64_pipe(oracle_mod):
         s.step(40)
         got = s.copy_out()
     assert np.array_equal(got, J.interior_of(oracle_mod.jacobi(u, 40)))
+
+
+def test_widen_f32_exhaustive():
+    # every binary32 bit pattern, on the device, bit for bit (NaN stays NaN)
+    assert jg.jacobi_selftest_widen() == 0

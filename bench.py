@@ -49,7 +49,8 @@ def parse_args():
                    help="step path; auto = the library's autotuner picks path and ring depth")
     p.add_argument("--iters", type=int, default=0, help="override the workload's iterations per step")
     p.add_argument("--e2e-steps", type=int, default=2)
-    p.add_argument("--cpu-iters", type=int, default=4, help="oracle iterations in the CPU sample")
+    p.add_argument("--cpu-iters", type=int, default=100,
+                   help="oracle iterations in the CPU sample (about 7 s on 16 Arm cores at 512^3)")
     p.add_argument("--no-sweep", action="store_true", help="skip the channel ping-pong sweep")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--serve-requests", type=int, default=200,
@@ -191,10 +192,12 @@ def workload_config(name, grids, splits, dtype, iters, path):
     return cfg
 
 
-def cpu_baseline(name, iters_sample):
+def cpu_baseline(name, iters_sample, single_thread=False):
     """The oracle as it stands on the host cores, on a bounded sample: the first
     `iters_sample` iterations of the workload (for a batch, of its first grids
-    up to about 64 M points)."""
+    up to about 64 M points).  With `single_thread`, also one iteration of the
+    first sampled grid on one core (the oracle's result does not depend on the
+    thread count)."""
     import jacobi_inputs as J
     import numpy as np
     import oracle
@@ -207,6 +210,8 @@ def cpu_baseline(name, iters_sample):
             break
         take.append((g, ini))
         pts += g[0] * g[1] * g[2]
+    # one untimed iteration first: thread start-up and first-touch page faults
+    oracle.jacobi(J.initial_grid(*take[0][0], dtype=npdt, **take[0][1]), 1)
     dt = 0.0
     for g, ini in take:
         u0 = J.initial_grid(*g, dtype=npdt, **ini)
@@ -216,9 +221,23 @@ def cpu_baseline(name, iters_sample):
     what = (f"{iters_sample} of {iters} iterations of the full {grids[0][0]}x{grids[0][1]}x{grids[0][2]} grid"
             if len(grids) == 1 else f"{iters_sample} of {iters} iterations of the first {len(take)} of "
                                     f"{len(grids)} grids ({pts / 1e6:.1f} M points)")
-    return {"value": pts * iters_sample / dt / 1e9, "unit": "GLUP/s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": what + ", monolithic C oracle, OpenMP over z-planes", "seconds": dt,
-            "lups": pts * iters_sample}
+    out = {"value": pts * iters_sample / dt / 1e9, "unit": "GLUP/s", "cores": oracle.threads(), "kind": "oracle",
+           "sample": what + ", monolithic C oracle, OpenMP over z-planes", "seconds": dt,
+           "lups": pts * iters_sample}
+    if single_thread:
+        g, ini = take[0]
+        u0 = J.initial_grid(*g, dtype=npdt, **ini)
+        cores = oracle.threads()
+        oracle.set_threads(1)
+        try:
+            t0 = time.perf_counter()
+            oracle.jacobi(u0, 1)
+            dt1 = time.perf_counter() - t0
+        finally:
+            oracle.set_threads(cores)
+        out["single_thread"] = {"value": g[0] * g[1] * g[2] / dt1 / 1e9, "unit": "GLUP/s", "cores": 1,
+                                "sample": f"1 iteration of the {g[0]}x{g[1]}x{g[2]} grid", "seconds": dt1}
+    return out
 
 
 def run_reference(args):
@@ -228,7 +247,7 @@ def run_reference(args):
     import jacobi_inputs as J
     grids, splits, _, dtype, iters = J.workload_grids(args.workload)
     for _ in range(args.warmup):
-        cpu_baseline(args.workload, args.cpu_iters)
+        cpu_baseline(args.workload, 1)
     secs, lups, cb = 0.0, 0, None
     for _ in range(args.steps):
         cb = cpu_baseline(args.workload, args.cpu_iters)
@@ -610,7 +629,7 @@ def run_ours(args):
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cb = cpu_baseline(args.workload, args.cpu_iters)
+        cb = cpu_baseline(args.workload, args.cpu_iters, single_thread=True)
         cb.pop("seconds", None)
         cb.pop("lups", None)
 

@@ -24,6 +24,15 @@
  *     CUDA kernels (sm_103a).  Calls that need a GPU fail with JACOBI_ECUDA
  *     when none is present.
  *
+ * Environment (read by jacobi_create and jacobi_autotune):
+ *   JACOBI_WAIT_MS     limit of every device-side wait in milliseconds (default
+ *                      1000); an expired wait ends the kernel with
+ *                      JACOBI_ETIMEDOUT instead of spinning on;
+ *   JACOBI_FP64_EMU=0  keeps every FP64 add on the FP64 pipe (see
+ *                      jacobi_selftest_dadd);
+ *   JACOBI_STAGES      ring depth (3..8) of the persistent kernel;
+ *   JACOBI_TUNE_CACHE  file that caches jacobi_autotune's choices.
+ *
  * Data layout of a grid of nx*ny*nz interior points ("interior" layout): one
  * array of nz*ny*nx values, x fastest.  The "padded" layout adds the
  * Dirichlet boundary: (nz+2)*(ny+2)*(nx+2) values, x fastest, interior at

@@ -316,8 +316,14 @@ int run_round(serve_s* s) {
 
 int retire_finished(serve_s* s) {
   const size_t nslot = s->slots.size();
+  uint32_t* h_err = (uint32_t*)(s->h_rec + nslot);  // the word after the records
   ENG_CUDA(cudaMemcpyAsync(s->h_rec, s->d_rec, nslot * sizeof(Record), cudaMemcpyDeviceToHost, s->stream));
+  ENG_CUDA(cudaMemcpyAsync(h_err, s->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream));
   ENG_CUDA(cudaStreamSynchronize(s->stream));
+  // A bounded wait that gave up inside a step leaves that round's iterates
+  // unreliable: stop the engine (pending requests then report the error).
+  if (*h_err != DEV_OK)
+    return set_error(JACOBI_ETIMEDOUT, "serve engine: a device-side wait gave up (code %u)", *h_err);
   for (int si : s->running) {
     Slot& sl = s->slots[si];
     const Record R = s->h_rec[si];
@@ -447,7 +453,7 @@ int serve_create(const serve_config* cfg, serve_t** out) {
   if (e == cudaSuccess) e = kind_fork_create(&s->fork);
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->dmem, off);
   if (e == cudaSuccess) e = cudaMemset(s->dmem, 0, off);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&s->h_rec, ns * sizeof(Record));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&s->h_rec, ns * sizeof(Record) + 64);  // + the error word
   if (e != cudaSuccess) {
     if (s->dmem) cudaFree(s->dmem);
     if (s->h_rec) cudaFreeHost(s->h_rec);

@@ -1,0 +1,75 @@
+"""Host-side pieces of bench.py (no GPU): the rule that ties committed ncu
+counters to the kernel sources they were taken from, the CPU baseline's
+sample, and the reference arm's JSON line at one rank."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def test_ncu_traffic_follows_the_source_hash(tmp_path, monkeypatch):
+    import bench
+    (tmp_path / "profiles").mkdir()
+    rec = {"workload": "w", "dram_bytes_per_launch": 123.0, "source_sha": "abc"}
+    (tmp_path / "profiles" / "ncu_step_w.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda: "abc")
+    assert bench.ncu_traffic("w")[0] == 123.0
+    # counters taken from other kernel sources are not reported
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda: "def")
+    assert bench.ncu_traffic("w")[0] is None
+    assert bench.ncu_traffic("missing") == (None, None)
+
+
+def test_kernel_source_hash_covers_the_step_kernel_sources(tmp_path, monkeypatch):
+    import shutil
+    import bench
+    csrc = tmp_path / "paper_2102_12416_gb300" / "csrc"
+    shutil.copytree(os.path.join(ROOT, "paper_2102_12416_gb300", "csrc"), csrc)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    base = bench.kernel_source_sha()
+    assert base == bench.kernel_source_sha()
+    for name in ("step.cu", "common.cuh", "kernels.cuh"):
+        p = csrc / name
+        text = p.read_text()
+        p.write_text(text + "\n")
+        assert bench.kernel_source_sha() != base, name
+        p.write_text(text)
+    assert bench.kernel_source_sha() == base
+    # host-only sources do not move it
+    (csrc / "api.cu").write_text((csrc / "api.cu").read_text() + "\n")
+    assert bench.kernel_source_sha() == base
+
+
+def test_cpu_baseline_sample():
+    import bench
+    cb = bench.cpu_baseline("jacobi3d-fp64-64c-2x2x2", 2, single_thread=True)
+    assert cb["kind"] == "oracle" and cb["unit"] == "GLUP/s" and cb["value"] > 0
+    assert cb["cores"] >= 1 and cb["lups"] == 2 * 64 ** 3
+    assert "2 of 100 iterations" in cb["sample"]
+    st = cb["single_thread"]
+    assert st["cores"] == 1 and st["value"] > 0
+
+
+def test_reference_arm_line_single_rank():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload",
+                          "jacobi3d-fp64-64c-2x2x2", "--steps", "2", "--warmup", "1", "--cpu-iters", "2"],
+                         cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 1
+    assert line["higher_is_better"] is True and line["unit"] == "GLUP/s" and line["dtype"] == "f64"
+    assert line["config"]["workload"] == "jacobi3d-fp64-64c-2x2x2"
+    assert line["e2e"] == {"value": line["value"], "unit": "GLUP/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["cpu_baseline"]["value"] == line["value"] and line["cpu_baseline"]["kind"] == "oracle"

@@ -9,6 +9,7 @@ The Jacobi iteration is the one the paper's proxy application runs
 (Sec. 4.3); the stencil and residual readings are stated in oracle/oracle.c.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -283,11 +284,28 @@ def test_faces_coordinates(oracle_mod):
 # Shared input generator
 # ---------------------------------------------------------------------------
 
+def _golden(name):
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+
+
 def test_splitmix64_published_vector():
-    """First outputs of SplitMix64 seeded with 1234567 (published test vector)."""
-    got = [int(x) for x in J.splitmix64(1234567, np.arange(5))]
-    assert got == [6457827717110365317, 3203168211198807973, 9817491932198370423,
-                   4593380528125082431, 16408922859458223821]
+    """First outputs of SplitMix64 seeded with 1234567 (published vector, cited
+    in the fixture)."""
+    want = [int(l) for l in open(_golden("splitmix64_seed1234567.txt")) if l.strip() and not l.startswith("#")]
+    got = [int(x) for x in J.splitmix64(1234567, np.arange(len(want)))]
+    assert len(want) == 5 and got == want
+
+
+def test_oracle_regression_fixtures(oracle_mod):
+    """The oracle reproduces its committed fixtures bit for bit (they were
+    written by tests/golden/make_golden.py, which calls only the oracle; a
+    change to the oracle's arithmetic has to rewrite them)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_golden", _golden("make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    for stem, grid, dtype, inputs, iters in mg.CASES:
+        assert mg.render(grid, dtype, inputs, iters) == open(_golden(stem + ".txt")).read(), stem
 
 
 def test_inputs_basic():

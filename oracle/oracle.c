@@ -22,7 +22,12 @@
  *  - Jacobi for the discrete Laplace equation: the new value is the mean of
  *    the six face neighbours, evaluated as
  *        s = ((u[i-1] + u[i+1]) + (u[j-1] + u[j+1])) + (u[k-1] + u[k+1])
- *        u' = s * c6,   c6 = the value of 1/6 rounded to the working type.
+ *    then, in FP64, u' = s * c6 with c6 = 1/6 rounded to double, and in FP32
+ *    u' = s / 6 rounded once to float.  Multiplying by the float nearest 1/6
+ *    would scale every FP32 update by 1 + 2^-25 (that float exceeds 1/6 by a
+ *    third of an ulp), a bias that accumulates over the iterations; the
+ *    double nearest 1/6 is off by 2^-55 relative, which stays far below the
+ *    FP64 rounding noise for any practical iteration count.
  *  - Residual (the paper runs without convergence checks; this is the
  *    convergence test the solver adds): r = s - 6*u at every interior point,
  *    evaluated in FP64 (FP32 states widened exactly), |r| = sqrt(sum r^2)
@@ -41,12 +46,16 @@
   ((((size_t)(k)) * (size_t)(ny + 2) + (size_t)(j)) * (size_t)(nx + 2) + (size_t)(i))
 
 static const double C6_F64 = 1.0 / 6.0; /* 1/6 rounded to nearest double */
-static const float C6_F32 = 1.0f / 6.0f; /* 1/6 rounded to nearest float */
 
-/* One Jacobi sweep over every interior point (Sec. 4.3): v <- N(u) * c6.
+/* The last operation of an update: FP64 multiplies by the double nearest 1/6,
+ * FP32 divides by 6 (IEEE division, one rounding). */
+#define FINISH_F64(s) ((s) * C6_F64)
+#define FINISH_F32(s) ((s) / 6.0f)
+
+/* One Jacobi sweep over every interior point (Sec. 4.3): v <- FINISH(N(u)).
  * v must already hold the boundary values; only interior points are written.
  * z-planes are independent, so the thread count never changes a value. */
-#define DEFINE_SWEEP(NAME, T, C6)                                               \
+#define DEFINE_SWEEP(NAME, T, FINISH)                                           \
   static void NAME(int64_t nx, int64_t ny, int64_t nz, const T* u, T* v) {      \
     _Pragma("omp parallel for schedule(static)")                              \
     for (int64_t k = 1; k <= nz; ++k) {                                         \
@@ -56,13 +65,13 @@ static const float C6_F32 = 1.0f / 6.0f; /* 1/6 rounded to nearest float */
           T sy = u[PIDX(i, j - 1, k)] + u[PIDX(i, j + 1, k)];                   \
           T sz = u[PIDX(i, j, k - 1)] + u[PIDX(i, j, k + 1)];                   \
           T s = (sx + sy) + sz;                                                 \
-          v[PIDX(i, j, k)] = s * C6;                                            \
+          v[PIDX(i, j, k)] = FINISH(s);                                         \
         }                                                                       \
       }                                                                         \
     }                                                                           \
   }
-DEFINE_SWEEP(sweep_f64, double, C6_F64)
-DEFINE_SWEEP(sweep_f32, float, C6_F32)
+DEFINE_SWEEP(sweep_f64, double, FINISH_F64)
+DEFINE_SWEEP(sweep_f32, float, FINISH_F32)
 
 /* n_iters Jacobi iterations in place on the padded array u.  Returns 0, or -1
  * when the scratch copy cannot be allocated. */

@@ -39,10 +39,12 @@
  * indices 1..n on each axis.
  *
  * Arithmetic (the paper prints no stencil; this is the library's reading):
- *   u'(i,j,k) = ((u(i-1)+u(i+1)) + (u(j-1)+u(j+1))) + (u(k-1)+u(k+1)),
- *   then multiplied by 1/6 rounded to the state type; every operation is
- *   rounded separately (no fused multiply-add), so an FP64 run is bit-exact
- *   with a monolithic CPU evaluation in the same order, for any block split.
+ *   s(i,j,k) = ((u(i-1)+u(i+1)) + (u(j-1)+u(j+1))) + (u(k-1)+u(k+1)),
+ *   then u' = s * RN(1/6) in FP64 and u' = RN(s / 6) in FP32 (the float
+ *   nearest 1/6 is a third of an ulp too large and would bias every FP32
+ *   update by 2^-25); every operation is rounded separately (no fused
+ *   multiply-add in the sum), so a run is bit-exact with a monolithic CPU
+ *   evaluation in the same order, for any block split.
  * Residual (an addition; the paper's Jacobi3D runs a fixed iteration count):
  *   r = s - 6u in FP64 at every interior point, |r| = sqrt(sum r^2), b the same
  *   expression with the interior set to zero, rel = |r| / |b|.
@@ -123,12 +125,34 @@ typedef struct { int32_t mode; int32_t pad_; int64_t x, y, z; } jacobi_split;
  *               the blocks (units) signal the units they share data with
  *               through release/acquire progress flags in device memory
  *               instead of kernel boundaries (bounded waits).
- *   GRAPH:      the FUSED launches captured once in a CUDA graph and replayed. */
+ *   GRAPH:      the FUSED launches captured once in a CUDA graph and replayed.
+ * The next three run the halo exchange the way the paper's host-driven
+ * runtimes do (Sec. 3, Sec. 4.3), for comparing the exchange forms on the
+ * Jacobi3D workload; each iteration is a stencil launch followed by the
+ * exchange, and the host takes part in every exchange:
+ *   CHANNEL:     Channel API form (Sec. 3.2.2): the host waits for the
+ *                stencil, then issues the sends; every receive slot was posted
+ *                in advance, so one launch packs each face of the new iterate
+ *                straight into the neighbour's slot.
+ *   MESSAGING:   GPU Messaging form (Sec. 3.2.1): each face is packed into its
+ *                block's send buffer; after the host has waited for that, a
+ *                metadata message per face (source address, size) goes through
+ *                a host-side mailbox of the receiving block, whose handler
+ *                posts the receive (the source -> slot copy); the posted copies
+ *                run as one launch from a table of descriptors uploaded by the
+ *                host.
+ *   HOST_STAGED: host staging, the non-GPU-aware form (Fig. 9): faces are
+ *                packed, copied device -> pinned host memory, the host waits
+ *                for them, then they are copied host -> device and unpacked into
+ *                the neighbours' slots. */
 typedef enum {
   JACOBI_PATH_FUSED = 0,
   JACOBI_PATH_EXPLICIT = 1,
   JACOBI_PATH_PERSISTENT = 2,
-  JACOBI_PATH_GRAPH = 3
+  JACOBI_PATH_GRAPH = 3,
+  JACOBI_PATH_CHANNEL = 4,
+  JACOBI_PATH_MESSAGING = 5,
+  JACOBI_PATH_HOST_STAGED = 6
 } jacobi_path;
 
 /* Solve outcome. */
@@ -168,6 +192,10 @@ typedef struct {
                             integer pipe (0 or 3) for grids inside the integer
                             adder's domain; the kernels send most of them there */
   int32_t pad_;
+  int32_t kind_items[8]; /* work items per step kernel variant: [0] tiles (rows
+                            too wide to stream); [1..3] plane streaming with 8,
+                            4, 2 consumer warps per CTA; [4..6] the same for
+                            blocks with padded (ragged) rows; [7] unused */
 } jacobi_info_t;
 
 /* Outcome of jacobi_autotune. */
@@ -266,6 +294,15 @@ int jacobi_copy_out(jacobi_t* h, int64_t grid, void* dst, int32_t dst_on_device,
  * halo exchange included, on the selected path.  Asynchronous. */
 int jacobi_step(jacobi_t* h, int64_t n_iters, void* stream);
 
+/* jacobi_step with the two phases of each iteration timed by CUDA events on
+ * `stream`: *compute_ms receives the summed time of the stencil launches and
+ * *exchange_ms the summed time from the end of each stencil launch to the end
+ * of that iteration's halo exchange (pack, transfer, host hand-offs and waits,
+ * unpack).  On FUSED, GRAPH and PERSISTENT the exchange is fused into the
+ * stencil: the whole iteration counts as compute and *exchange_ms is 0.
+ * Synchronises the stream. */
+int jacobi_step_timed(jacobi_t* h, int64_t n_iters, void* stream, double* compute_ms, double* exchange_ms);
+
 /* FP64 residual of the current iterate of every grid: rel[g] = |b-Au|/|b|,
  * abs[g] = |b-Au| (either pointer may be NULL; arrays of n_grids doubles in
  * host memory).  Partials are reduced in a fixed order, so results are
@@ -312,6 +349,17 @@ int jacobi_selftest_dadd(const double* a, const double* b, int64_t n, double* ou
  * Expected 0.  Synchronises the stream. */
 int jacobi_selftest_widen(uint64_t* mismatches, void* stream);
 
+/* Test support for the FP32 update's division: u' = RN(s / 6) is computed as
+ * RN(s * zh + RN(s * zl)) with zh = RN(1/6), zl = RN(1/6 - zh) (a method of
+ * Brisebarre, Muller and Raina for division by a constant; the paper prints no
+ * stencil, see the arithmetic note at the top of this file), with the
+ * division instruction sequence for the inputs outside that form's proven
+ * domain.  Runs all 2^32 binary32 bit patterns through it on the device and
+ * writes to *mismatches (host) how many differ bit for bit from the division
+ * instruction sequence (NaN inputs must give a NaN).  Expected 0.
+ * Synchronises the stream; allocates 8 bytes of scratch. */
+int jacobi_selftest_div6(uint64_t* mismatches, void* stream);
+
 /* Measured issue rates of this GPU's two add pipes (for rooflines): FP64 adds
  * per second on the FP64 pipe, and FP64 adds per second through the
  * integer-pipe routine of jacobi_selftest_dadd; each from one timed launch of
@@ -325,16 +373,28 @@ int jacobi_pipe_rates(double* fp64_adds_per_s, double* int_adds_per_s, void* str
  * clears the injection. */
 int jacobi_debug_drop_block(jacobi_t* h, int64_t block);
 
+/* Measurement switch for the halo share of a step (the share of step time
+ * that exchanging halos between blocks costs): with on = 1 every block stores
+ * its new boundary planes into its OWN receive slots instead of its
+ * neighbours' (same kernels, same bytes, same slot shapes, but each block then
+ * reads its own faces as ghosts), so timing a step with and without it shows
+ * what routing the faces to other blocks costs.  The iterates computed while
+ * it is on are NOT Jacobi iterates of the grid; switching it off restores the
+ * exchange, not the state (reset the state with jacobi_set_state).
+ * Synchronises the device. */
+int jacobi_measure_local_halo(jacobi_t* h, int32_t on);
+
 /* ---- allocation-free residual ------------------------------------------------- */
 
 /* Largest nz accepted by jacobi_residual_noalloc (size of its fixed scratch). */
 #define JACOBI_NOALLOC_MAX_PLANES 16384
 
 /* The paper has no counterpart to this call; it serves callers that cannot
- * allocate device memory when they need a residual: code running while a
- * stream is being captured into a CUDA graph (an allocation there is not a
- * stream operation and breaks or is refused by the capture), and applications
- * that reserve all device memory at start-up and forbid later allocations.
+ * allocate device memory when they need a residual: applications that
+ * reserve all device memory at start-up and forbid later allocations (a fixed
+ * footprint, or a framework whose caching allocator must account for every
+ * byte), and loops that cannot afford the device-wide synchronisation a
+ * cudaMalloc or cudaFree may bring.
  *
  * Computes the FP64 residual of a caller-owned padded state array u_padded
  * (device memory, (nz+2)*(ny+2)*(nx+2) values of `dtype`, x fastest, boundary
@@ -365,26 +425,48 @@ int channel_open(jacobi_t* h, uint32_t channel_id, int64_t block_a, int64_t bloc
                  size_t max_bytes, channel_t** out);
 
 /* Send `bytes` from device buffer src (16-byte aligned) on behalf of endpoint
- * `from_block` into the peer's receive slot, then publish the message's
- * sequence number with a release store.  Waits on the device (bounded) until
- * the peer has consumed the message that used the same slot two sends ago.
- * Asynchronous; a failed wait is reported by channel_sync. */
+ * `from_block`.  When the peer posted the matching receive earlier (see
+ * channel_recv), one launch copies the payload straight into the posted
+ * buffer and completes that receive (JACOBI_ESEQ at once, nothing sent, if the
+ * posted size differs).  Otherwise the payload goes into the peer's receive
+ * slot and the message's sequence number is published with a release store;
+ * the send waits on the device (bounded) until the peer has consumed the
+ * message that used the same slot two sends ago.  Asynchronous; a failed wait
+ * is reported by channel_sync. */
 int channel_send(channel_t* ch, int64_t from_block, const void* src, size_t bytes, void* stream);
 
-/* Receive the next message for endpoint `at_block`: acquire-wait (bounded)
- * until its sequence number is published, copy it to dst (device, 16-byte
- * aligned), or leave it in the slot when dst is NULL (zero-copy; see
- * channel_slot), then mark it consumed.  `bytes` must equal the sent size
- * (JACOBI_ESEQ otherwise, reported by channel_sync).  Asynchronous.  A receive
- * with no matching send in stream order times out with JACOBI_ETIMEDOUT. */
+/* Receive the next message for endpoint `at_block`.
+ *  - Posted receive: with dst (device, 16-byte aligned) given before the
+ *    matching channel_send has been issued (host program order), the call only
+ *    registers dst; the send delivers the payload straight into it (the
+ *    Channel API's pre-posted receive, Sec. 3.2.2).  Work that reads dst must
+ *    be ordered after that send (same stream, or an event).  Until then
+ *    channel_sync reports JACOBI_EAGAIN.
+ *  - Otherwise: acquire-wait on the device (bounded) until the message's
+ *    sequence number is published, then copy it to dst and mark it consumed,
+ *    or, with dst NULL (zero-copy), leave it in its slot (see channel_slot).
+ *    A zero-copy message holds its slot until the next channel_recv at this
+ *    endpoint or channel_release, both of which must be ordered after every
+ *    read of the slot; the peer's send of the message after next waits for
+ *    that release.
+ * `bytes` must equal the sent size (JACOBI_ESEQ otherwise, reported by
+ * channel_sync).  Asynchronous.  A waiting receive with no matching send
+ * earlier in stream order times out with JACOBI_ETIMEDOUT.  After channel_sync
+ * has reported JACOBI_ETIMEDOUT or JACOBI_ESEQ the channel's message counters
+ * no longer match: close and reopen it. */
 int channel_recv(channel_t* ch, int64_t at_block, void* dst, size_t bytes, void* stream);
+
+/* Release the slot held by the last zero-copy receive at endpoint at_block
+ * (no-op when none is held).  Asynchronous; order it after the reads. */
+int channel_release(channel_t* ch, int64_t at_block, void* stream);
 
 /* Device address of endpoint at_block's receive slot for message parity
  * `parity` (message n uses parity n & 1). */
 int channel_slot(channel_t* ch, int64_t at_block, int32_t parity, void** slot);
 
 /* Synchronise `stream` and report the first device-side failure of the
- * channel (JACOBI_ETIMEDOUT, JACOBI_ESEQ) or JACOBI_OK; clears it. */
+ * channel (JACOBI_ETIMEDOUT, JACOBI_ESEQ; clears it), else JACOBI_EAGAIN while
+ * a posted receive still waits for its send, else JACOBI_OK. */
 int channel_sync(channel_t* ch, void* stream);
 
 /* OSU-style ping-pong between the two endpoints (Sec. 4.2.1), run entirely on

@@ -30,13 +30,16 @@ JACOBI_BC_LINEAR, JACOBI_BC_LINEAR_NOISE, JACOBI_BC_UNIFORM = 0, 1, 2
 JACOBI_INTERIOR_ZERO, JACOBI_INTERIOR_UNIFORM, JACOBI_INTERIOR_BC = 0, 1, 2
 JACOBI_SPLIT_COUNT, JACOBI_SPLIT_SHAPE = 0, 1
 JACOBI_PATH_FUSED, JACOBI_PATH_EXPLICIT, JACOBI_PATH_PERSISTENT, JACOBI_PATH_GRAPH = 0, 1, 2, 3
+JACOBI_PATH_CHANNEL, JACOBI_PATH_MESSAGING, JACOBI_PATH_HOST_STAGED = 4, 5, 6
 JACOBI_SOLVE_CONVERGED, JACOBI_SOLVE_MAX_ITERS, JACOBI_SOLVE_STAGNATED = 0, 1, 2
 JACOBI_LAYOUT_INTERIOR, JACOBI_LAYOUT_PADDED = 0, 1
 JACOBI_MAX_BLOCK_EXTENT = 32764
 FACES = ("xm", "xp", "ym", "yp", "zm", "zp")
 
 PATHS = {"fused": JACOBI_PATH_FUSED, "explicit": JACOBI_PATH_EXPLICIT,
-         "persistent": JACOBI_PATH_PERSISTENT, "graph": JACOBI_PATH_GRAPH}
+         "persistent": JACOBI_PATH_PERSISTENT, "graph": JACOBI_PATH_GRAPH,
+         "channel": JACOBI_PATH_CHANNEL, "messaging": JACOBI_PATH_MESSAGING,
+         "host_staged": JACOBI_PATH_HOST_STAGED}
 PATH_NAMES = {v: k for k, v in PATHS.items()}
 DTYPES = {"f64": JACOBI_F64, "f32": JACOBI_F32}
 NP_DTYPES = {JACOBI_F64: np.float64, JACOBI_F32: np.float32}
@@ -66,7 +69,8 @@ class jacobi_info_t(ctypes.Structure):
     _fields_ = [("n_grids", c_int64), ("n_blocks", c_int64), ("n_points", c_int64),
                 ("iteration", c_int64), ("dtype", c_int32), ("path", c_int32),
                 ("halo_bytes_per_iter", c_int64), ("workspace_bytes", c_size_t), ("stages", c_int32),
-                ("item_kinds", c_int32), ("fp64_int_adds", c_int32), ("pad_", c_int32)]
+                ("item_kinds", c_int32), ("fp64_int_adds", c_int32), ("pad_", c_int32),
+                ("kind_items", c_int32 * 8)]
 
 
 class jacobi_tune_result(ctypes.Structure):
@@ -121,19 +125,23 @@ _SIGS = {
     "jacobi_copy_out": (ctypes.c_int, [P, c_int64, P, c_int32, c_int32, P]),
     "jacobi_step": (ctypes.c_int, [P, c_int64, P]),
     "jacobi_residual": (ctypes.c_int, [P, P, P, P]),
+    "jacobi_step_timed": (ctypes.c_int, [P, c_int64, P, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     "jacobi_solve": (ctypes.c_int, [P, c_double, c_int64, c_int64, c_int64, P, P, P, P]),
     "jacobi_sync": (ctypes.c_int, [P, P]),
     "jacobi_autotune": (ctypes.c_int, [P, c_int64, P, ctypes.POINTER(jacobi_tune_result)]),
     "jacobi_read_face": (ctypes.c_int, [P, c_int64, c_int32, P, P]),
     "jacobi_debug_drop_block": (ctypes.c_int, [P, c_int64]),
+    "jacobi_measure_local_halo": (ctypes.c_int, [P, c_int32]),
     "jacobi_selftest_dadd": (ctypes.c_int, [P, P, c_int64, P, P]),
     "jacobi_selftest_widen": (ctypes.c_int, [P, P]),
+    "jacobi_selftest_div6": (ctypes.c_int, [P, P]),
     "jacobi_pipe_rates": (ctypes.c_int, [ctypes.POINTER(c_double), ctypes.POINTER(c_double), P]),
     "jacobi_residual_noalloc": (ctypes.c_int, [P, jacobi_dim3, ctypes.c_int, P, P]),
     "channel_open": (ctypes.c_int, [P, c_uint32, c_int64, c_int64, c_size_t, ctypes.POINTER(P)]),
     "channel_send": (ctypes.c_int, [P, c_int64, P, c_size_t, P]),
     "channel_recv": (ctypes.c_int, [P, c_int64, P, c_size_t, P]),
     "channel_slot": (ctypes.c_int, [P, c_int64, c_int32, ctypes.POINTER(P)]),
+    "channel_release": (ctypes.c_int, [P, c_int64, P]),
     "channel_sync": (ctypes.c_int, [P, P]),
     "channel_pingpong": (ctypes.c_int, [P, c_size_t, c_int64, c_int32, P]),
     "channel_close": (ctypes.c_int, [P]),
@@ -292,6 +300,13 @@ def jacobi_step(h, n_iters, stream=None):
     _call("jacobi_step", h, n_iters, _stream(stream))
 
 
+def jacobi_step_timed(h, n_iters, stream=None):
+    """(compute_ms, exchange_ms) summed over n_iters iterations (see include/jacobi.h)."""
+    a, b = c_double(), c_double()
+    _call("jacobi_step_timed", h, n_iters, _stream(stream), ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
 def jacobi_residual(h, n_grids, stream=None):
     rel = (c_double * n_grids)()
     ab = (c_double * n_grids)()
@@ -334,11 +349,23 @@ def jacobi_selftest_widen(stream=None):
     return n.value
 
 
+def jacobi_selftest_div6(stream=None):
+    """Number of binary32 inputs whose FP32-update division RN(s / 6) differs
+    from the division instruction sequence (all 2^32 bit patterns, on the device)."""
+    n = ctypes.c_uint64(0)
+    _call("jacobi_selftest_div6", ctypes.addressof(n), _stream(stream))
+    return n.value
+
+
 def jacobi_pipe_rates(stream=None):
     """(FP64-pipe adds/s, integer-pipe FP64 adds/s) measured on the current GPU."""
     a, b = c_double(), c_double()
     _call("jacobi_pipe_rates", ctypes.byref(a), ctypes.byref(b), _stream(stream))
     return a.value, b.value
+
+
+def jacobi_measure_local_halo(h, on):
+    _call("jacobi_measure_local_halo", h, 1 if on else 0)
 
 
 def jacobi_debug_drop_block(h, block):
@@ -367,6 +394,10 @@ def channel_send(ch, from_block, src, nbytes, stream=None):
 
 def channel_recv(ch, at_block, dst, nbytes, stream=None):
     _call("channel_recv", ch, at_block, None if dst is None else int(dst), nbytes, _stream(stream))
+
+
+def channel_release(ch, at_block, stream=None):
+    _call("channel_release", ch, at_block, _stream(stream))
 
 
 def channel_slot(ch, at_block, parity) -> int:
@@ -492,6 +523,10 @@ class Jacobi3D:
     def step(self, n):
         jacobi_step(self.h, n, self.stream)
 
+    def step_timed(self, n):
+        """Advance n iterations; returns (compute_ms, exchange_ms) for the whole call."""
+        return jacobi_step_timed(self.h, n, self.stream)
+
     def sync(self):
         jacobi_sync(self.h, self.stream)
 
@@ -502,6 +537,12 @@ class Jacobi3D:
 
     def launch_kinds(self) -> int:
         return max(1, self.info.item_kinds)
+
+    def kind_items(self) -> dict:
+        """Work items per step kernel variant (non-empty ones only)."""
+        names = ("tiles", "stream8", "stream4", "stream2", "stream8_ragged", "stream4_ragged", "stream2_ragged")
+        ki = self.info.kind_items
+        return {n: ki[k] for k, n in enumerate(names) if ki[k]}
 
     def residual(self):
         return jacobi_residual(self.h, len(self.grids), self.stream)

@@ -306,6 +306,7 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
   P->off_punit_ids = take(nu * sizeof(int32_t));
   P->off_pdep_off = take((nu + 1) * sizeof(int32_t));
   P->off_pdep_ids = take(8 * nu * sizeof(int32_t));
+  P->off_active_blocks = take(nb * sizeof(int32_t));
   const size_t per16 = 32;  // plane pitch rounded to 32 elements
   for (auto& B : P->blocks) {
     B.pitch = (int64_t)align_up((size_t)(B.rx * B.ry), per16);
@@ -320,20 +321,23 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
         B.recv_off[f][0] = take(fb);
         B.recv_off[f][1] = take(fb);
         P->halo_elems += face_points_host(B, f);
+        P->halo_faces += 1;
       } else {
         B.recv_off[f][0] = B.recv_off[f][1] = take(fb);
       }
     }
   }
+  P->off_stage_begin = off;
   for (auto& B : P->blocks)
     for (int f = 0; f < 6; ++f)
       B.stage_off[f] = B.nbr[f] >= 0 ? take((size_t)face_elems_host(B, f) * P->elem) : 0;
+  P->off_stage_end = off;
   P->bytes = off;
   return JACOBI_OK;
 }
 
 void fill_block_tables(const Plan& P, char* ws, int64_t base, int32_t grid_override, BlockDev* bd, BlockGeom* geo,
-                       void** stage_tab) {
+                       void** stage_tab, bool local_halo) {
   const int64_t nb = (int64_t)P.blocks.size();
   for (int64_t b = 0; b < nb; ++b) {
     const BlockHost& B = P.blocks[b];
@@ -347,8 +351,10 @@ void fill_block_tables(const Plan& P, char* ws, int64_t base, int32_t grid_overr
       D.nbr[f] = B.nbr[f] >= 0 ? (int32_t)(base + B.nbr[f]) : -1;
       if (B.nbr[f] >= 0) {
         const BlockHost& N = P.blocks[B.nbr[f]];
-        D.send[f][0] = ws + N.recv_off[opposite(f)][0];
-        D.send[f][1] = ws + N.recv_off[opposite(f)][1];
+        // (the own slot of face f has the same shape as the neighbour's slot
+        // of the opposite face: both span the face the blocks share)
+        D.send[f][0] = ws + (local_halo ? B.recv_off[f][0] : N.recv_off[opposite(f)][0]);
+        D.send[f][1] = ws + (local_halo ? B.recv_off[f][1] : N.recv_off[opposite(f)][1]);
         if (stage_tab) stage_tab[b * 6 + f] = ws + B.stage_off[f];
       }
     }
@@ -378,7 +384,7 @@ int upload_tables(jacobi_t* h, cudaStream_t s) {
   std::vector<BlockDev> bd(nb);
   std::vector<BlockGeom> geo(nb);
   std::vector<void*> stab(nb * 6, nullptr);
-  fill_block_tables(P, h->ws, 0, -1, bd.data(), geo.data(), stab.data());
+  fill_block_tables(P, h->ws, 0, -1, bd.data(), geo.data(), stab.data(), h->local_halo);
   const int64_t ng = (int64_t)P.grids.size();
   std::vector<InitDev> ini(ng);
   std::vector<int32_t> gids(ng);
@@ -423,6 +429,7 @@ int refresh_active(jacobi_t* h, cudaStream_t s) {
   h->active_dep_off.clear();
   h->active_deps.clear();
   h->active_grids.clear();
+  h->active_blocks.clear();
   // Persistent-kernel units: the z-chunks of each block (items are ordered by
   // z-chunk within a block).  Unit (b, c) at iteration it needs iteration
   // it - 1 finished by the units it shares data with, both ways (reads of
@@ -438,6 +445,7 @@ int refresh_active(jacobi_t* h, cudaStream_t s) {
     const GridHost& G = P.grids[g];
     if (!G.active) continue;
     h->active_grids.push_back((int32_t)g);
+    for (int64_t b = G.block_begin; b < G.block_end; ++b) h->active_blocks.push_back((int32_t)b);
     for (int64_t b = G.block_begin; b < G.block_end; ++b) {
       if (b == h->drop_block && h->path == JACOBI_PATH_PERSISTENT) continue;  // injected fault
       const BlockHost& B = P.blocks[b];
@@ -474,6 +482,9 @@ int refresh_active(jacobi_t* h, cudaStream_t s) {
     JGB_CUDA(cudaMemcpyAsync(h->d_kind, h->kind_items.data(), h->kind_items.size() * sizeof(WorkItem),
                              cudaMemcpyHostToDevice, s));
   }
+  if (!h->active_blocks.empty())
+    JGB_CUDA(cudaMemcpyAsync(h->d_active_blocks, h->active_blocks.data(), h->active_blocks.size() * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, s));
   if (!h->active_units.empty()) {
     auto up = [&](int32_t* d, const std::vector<int32_t>& v) {
       return cudaMemcpyAsync(d, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
@@ -608,14 +619,98 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
   return JACOBI_OK;
 }
 
-int step_explicit(jacobi_t* h, int64_t it0, int64_t n, cudaStream_t s) {
+// The halo exchange that follows the stencil launch of iteration `it` on the
+// unfused paths (the new iterate has parity p ^ 1 of each grid's own count):
+//   EXPLICIT:    device-side pack into the staging buffers, device-side copy
+//                into the neighbours' slots (no host step);
+//   CHANNEL:     the host waits for the stencil, then one launch packs every
+//                face straight into the neighbour's pre-posted slot;
+//   MESSAGING:   pack into the staging buffers (the send buffers); the host
+//                waits, routes one metadata message per face through the
+//                receiving block's mailbox, and each receiver posts its copy
+//                (source from the message, destination its own slot); the
+//                posted copies run as one launch from an uploaded descriptor
+//                table;
+//   HOST_STAGED: pack, copy the staging buffers device -> pinned host, the
+//                host waits for them, copy them host -> device, unpack into the
+//                neighbours' slots.
+int exchange(jacobi_t* h, int64_t it, cudaStream_t s) {
+  const Plan& P = h->plan;
+  const int32_t na = (int32_t)h->active_blocks.size();
+  const int32_t* ids = h->d_active_blocks;
+  switch (h->path) {
+    case JACOBI_PATH_EXPLICIT:
+      JGB_CUDA(launch_pack_faces(h->d_blocks, ids, na, h->d_stage_tab, h->d_grids, it, P.dtype, s));
+      JGB_CUDA(launch_copy_faces(h->d_blocks, ids, na, h->d_stage_tab, h->d_grids, it, P.dtype, s));
+      return JACOBI_OK;
+    case JACOBI_PATH_CHANNEL:
+      JGB_CUDA(cudaStreamSynchronize(s));
+      JGB_CUDA(launch_pack_faces(h->d_blocks, ids, na, h->d_stage_tab, h->d_grids, it, P.dtype, s, true));
+      return JACOBI_OK;
+    case JACOBI_PATH_MESSAGING: {
+      JGB_CUDA(launch_pack_faces(h->d_blocks, ids, na, h->d_stage_tab, h->d_grids, it, P.dtype, s));
+      if (!h->d_desc) {
+        const size_t n = (size_t)std::max<int64_t>(P.halo_faces, 1);
+        JGB_CUDA(cudaMalloc((void**)&h->d_desc, n * sizeof(CopyDesc)));
+        JGB_CUDA(cudaMallocHost((void**)&h->h_desc, n * sizeof(CopyDesc)));
+        h->mailbox.assign(P.blocks.size(), {});
+      }
+      JGB_CUDA(cudaStreamSynchronize(s));  // the send buffers are ready: post the metadata
+      for (int32_t b : h->active_blocks) {
+        const BlockHost& B = P.blocks[b];
+        for (int f = 0; f < 6; ++f)
+          if (B.nbr[f] >= 0)
+            h->mailbox[B.nbr[f]].push_back(jacobi_s::HaloMeta{h->ws + B.stage_off[f],
+                                                               face_elems_host(B, f) * (int64_t)P.elem,
+                                                               opposite(f)});
+      }
+      int32_t nd = 0;
+      for (int32_t r : h->active_blocks) {  // each receiver handles its messages
+        const BlockHost& R = P.blocks[r];
+        const int pn = (int)((it - P.grids[R.grid].start_iter + 1) & 1);
+        for (const jacobi_s::HaloMeta& m : h->mailbox[r]) {
+          if (m.bytes != face_elems_host(R, m.face) * (int64_t)P.elem)
+            return set_error(JACOBI_ESEQ, "halo message of %lld bytes for a %lld-byte slot", (long long)m.bytes,
+                             (long long)(face_elems_host(R, m.face) * (int64_t)P.elem));
+          h->h_desc[nd++] = CopyDesc{m.src, h->ws + R.recv_off[m.face][pn], m.bytes};
+        }
+        h->mailbox[r].clear();
+      }
+      JGB_CUDA(cudaMemcpyAsync(h->d_desc, h->h_desc, (size_t)nd * sizeof(CopyDesc), cudaMemcpyHostToDevice, s));
+      JGB_CUDA(launch_copy_desc(h->d_desc, nd, s));
+      // the pinned descriptor table is rewritten by the next exchange only
+      // after its stream synchronisation, which follows this copy
+      return JACOBI_OK;
+    }
+    case JACOBI_PATH_HOST_STAGED: {
+      const size_t bytes = P.off_stage_end - P.off_stage_begin;
+      JGB_CUDA(launch_pack_faces(h->d_blocks, ids, na, h->d_stage_tab, h->d_grids, it, P.dtype, s));
+      if (bytes == 0) return JACOBI_OK;
+      if (!h->h_halo) JGB_CUDA(cudaMallocHost(&h->h_halo, bytes));
+      JGB_CUDA(cudaMemcpyAsync(h->h_halo, h->ws + P.off_stage_begin, bytes, cudaMemcpyDeviceToHost, s));
+      JGB_CUDA(cudaStreamSynchronize(s));  // the faces are in host memory: hand them on
+      JGB_CUDA(cudaMemcpyAsync(h->ws + P.off_stage_begin, h->h_halo, bytes, cudaMemcpyHostToDevice, s));
+      JGB_CUDA(launch_copy_faces(h->d_blocks, ids, na, h->d_stage_tab, h->d_grids, it, P.dtype, s));
+      return JACOBI_OK;
+    }
+    default:
+      return set_error(JACOBI_EINVAL, "path %d has no separate exchange", h->path);
+  }
+}
+
+// Stencil launch + exchange per iteration on the unfused paths.  With `ev`
+// (2n + 1 events) ev[2t] / ev[2t + 1] / ev[2t + 2] bracket iteration t's
+// stencil and exchange on the stream.
+int step_exchange(jacobi_t* h, int64_t it0, int64_t n, cudaStream_t s, cudaEvent_t* ev = nullptr) {
   StepLaunch a = step_args(h, 0, false);
-  const int32_t nb = (int32_t)h->plan.blocks.size();
+  if (ev) JGB_CUDA(cudaEventRecord(ev[0], s));
   for (int64_t t = 0; t < n; ++t) {
     a.it = it0 + t;
     JGB_CUDA(launch_step(a, kWrite, s, &h->fork));
-    JGB_CUDA(launch_pack_faces(h->d_blocks, nb, h->d_stage_tab, h->d_grids, a.it, h->plan.dtype, s));
-    JGB_CUDA(launch_copy_faces(h->d_blocks, nb, h->d_stage_tab, h->d_grids, a.it, h->plan.dtype, s));
+    if (ev) JGB_CUDA(cudaEventRecord(ev[2 * t + 1], s));
+    int rc = exchange(h, a.it, s);
+    if (rc) return rc;
+    if (ev) JGB_CUDA(cudaEventRecord(ev[2 * t + 2], s));
   }
   return JACOBI_OK;
 }
@@ -632,7 +727,10 @@ int do_step(jacobi_t* h, int64_t n, cudaStream_t s) {
     case JACOBI_PATH_FUSED: rc = step_fused_direct(h, h->iter, n, s); break;
     case JACOBI_PATH_GRAPH: rc = step_graph(h, h->iter, n, s); break;
     case JACOBI_PATH_PERSISTENT: rc = step_persistent(h, h->iter, n, false, s); break;
-    case JACOBI_PATH_EXPLICIT: rc = step_explicit(h, h->iter, n, s); break;
+    case JACOBI_PATH_EXPLICIT:
+    case JACOBI_PATH_CHANNEL:
+    case JACOBI_PATH_MESSAGING:
+    case JACOBI_PATH_HOST_STAGED: rc = step_exchange(h, h->iter, n, s); break;
     default: return set_error(JACOBI_EINVAL, "bad path");
   }
   if (rc) return rc;
@@ -871,6 +969,7 @@ int jacobi_create_batch(int64_t n_grids, const jacobi_dim3* grids, const jacobi_
   h->d_punit_ids = (int32_t*)(h->ws + P.off_punit_ids);
   h->d_pdep_off = (int32_t*)(h->ws + P.off_pdep_off);
   h->d_pdep_ids = (int32_t*)(h->ws + P.off_pdep_ids);
+  h->d_active_blocks = (int32_t*)(h->ws + P.off_active_blocks);
   if (const char* w = getenv("JACOBI_WAIT_MS")) {
     const double ms = atof(w);
     if (ms > 0) h->wait_ns = (uint64_t)(ms * 1e6);
@@ -913,6 +1012,9 @@ int jacobi_destroy(jacobi_t* h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
   kind_fork_destroy(&h->fork);
   if (h->stage) cudaFree(h->stage);
+  if (h->d_desc) cudaFree(h->d_desc);
+  if (h->h_desc) cudaFreeHost(h->h_desc);
+  if (h->h_halo) cudaFreeHost(h->h_halo);
   if (h->own_ws && h->ws) cudaFree(h->ws);
   if (h->h_grids) cudaFreeHost(h->h_grids);
   if (h->h_norms) cudaFreeHost(h->h_norms);
@@ -936,6 +1038,7 @@ int jacobi_info(const jacobi_t* h, jacobi_info_t* out) {
   int kinds = 0;
   for (int k = 0; k < kItemKinds; ++k) kinds += h->kind_off[k + 1] > h->kind_off[k] ? 1 : 0;
   out->item_kinds = kinds;
+  for (int k = 0; k < 8; ++k) out->kind_items[k] = k < kItemKinds ? h->kind_off[k + 1] - h->kind_off[k] : 0;
   return JACOBI_OK;
 }
 
@@ -1081,7 +1184,7 @@ int jacobi_block(const jacobi_t* h, int64_t block, jacobi_block_info* out) {
 }
 
 int jacobi_set_path(jacobi_t* h, int32_t path) {
-  if (!h || path < JACOBI_PATH_FUSED || path > JACOBI_PATH_GRAPH) return set_error(JACOBI_EINVAL, "bad path");
+  if (!h || path < JACOBI_PATH_FUSED || path > JACOBI_PATH_HOST_STAGED) return set_error(JACOBI_EINVAL, "bad path");
   if (h->path != path) h->tables_dirty = true;
   h->path = path;
   return JACOBI_OK;
@@ -1097,6 +1200,54 @@ int jacobi_step(jacobi_t* h, int64_t n_iters, void* stream) {
     cudaError_t q = cudaStreamQuery(s);
     if (q != cudaSuccess && q != cudaErrorNotReady) return set_error(JACOBI_ECUDA, "%s", cudaGetErrorString(q));
   }
+  return JACOBI_OK;
+}
+
+int jacobi_step_timed(jacobi_t* h, int64_t n_iters, void* stream, double* compute_ms, double* exchange_ms) {
+  if (!h || n_iters < 0 || n_iters > (1 << 20)) return set_error(JACOBI_EINVAL, "bad arguments to jacobi_step_timed");
+  const cudaStream_t s = S(stream);
+  int rc = refresh_active(h, s);
+  if (rc) return rc;
+  const bool split = h->path == JACOBI_PATH_EXPLICIT || h->path == JACOBI_PATH_CHANNEL ||
+                     h->path == JACOBI_PATH_MESSAGING || h->path == JACOBI_PATH_HOST_STAGED;
+  const int64_t n = (split && !h->active_items.empty()) ? n_iters : 0;
+  std::vector<cudaEvent_t> ev(split ? 2 * n + 1 : 2, nullptr);
+  auto destroy = [&]() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  };
+  for (cudaEvent_t& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      e = nullptr;
+      destroy();
+      return set_error(JACOBI_ECUDA, "event creation failed");
+    }
+  double comp = 0.0, exch = 0.0;
+  if (split) {
+    rc = step_exchange(h, h->iter, n, s, n > 0 ? ev.data() : nullptr);
+    if (!rc) h->iter += n_iters;
+    if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = set_error(JACOBI_ECUDA, "stream synchronisation failed");
+    for (int64_t t = 0; t < n && !rc; ++t) {
+      float a = 0.f, b = 0.f;
+      cudaEventElapsedTime(&a, ev[2 * t], ev[2 * t + 1]);
+      cudaEventElapsedTime(&b, ev[2 * t + 1], ev[2 * t + 2]);
+      comp += a;
+      exch += b;
+    }
+  } else {
+    if (cudaEventRecord(ev[0], s) != cudaSuccess) rc = set_error(JACOBI_ECUDA, "event record failed");
+    if (!rc) rc = do_step(h, n_iters, s);
+    if (!rc && cudaEventRecord(ev[1], s) != cudaSuccess) rc = set_error(JACOBI_ECUDA, "event record failed");
+    if (!rc && cudaEventSynchronize(ev[1]) != cudaSuccess) rc = set_error(JACOBI_ECUDA, "event wait failed");
+    float a = 0.f;
+    if (!rc) cudaEventElapsedTime(&a, ev[0], ev[1]);
+    comp = a;
+    if (!rc && h->path == JACOBI_PATH_PERSISTENT) rc = check_err_word(h, s);
+  }
+  destroy();
+  if (rc) return rc;
+  if (compute_ms) *compute_ms = comp;
+  if (exchange_ms) *exchange_ms = exch;
   return JACOBI_OK;
 }
 
@@ -1257,6 +1408,22 @@ int jacobi_selftest_widen(uint64_t* mismatches, void* stream) {
   return JACOBI_OK;
 }
 
+int jacobi_selftest_div6(uint64_t* mismatches, void* stream) {
+  if (!mismatches) return set_error(JACOBI_EINVAL, "null pointer");
+  const cudaStream_t s = S(stream);
+  unsigned long long* d = nullptr;
+  JGB_CUDA(cudaMalloc((void**)&d, sizeof *d));
+  unsigned long long n = 0;
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof *d, s);
+  if (e == cudaSuccess) e = launch_selftest_div6(d, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&n, d, sizeof n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  if (e != cudaSuccess) return set_error(JACOBI_ECUDA, "division self-test failed: %s", cudaGetErrorString(e));
+  *mismatches = (uint64_t)n;
+  return JACOBI_OK;
+}
+
 int jacobi_selftest_dadd(const double* a, const double* b, int64_t n, double* out, void* stream) {
   if ((!a || !b || !out) && n > 0) return set_error(JACOBI_EINVAL, "null pointer");
   if (n < 0) return set_error(JACOBI_EINVAL, "negative count");
@@ -1316,6 +1483,21 @@ int jacobi_read_face(jacobi_t* h, int64_t block, int32_t face, void* dst, void* 
   JGB_CUDA(cudaMemcpy2DAsync(dst, width * e, h->ws + B.recv_off[face][parity], pitch * e, width * e, height,
                              cudaMemcpyDeviceToHost, S(stream)));
   JGB_CUDA(cudaStreamSynchronize(S(stream)));
+  return JACOBI_OK;
+}
+
+int jacobi_measure_local_halo(jacobi_t* h, int32_t on) {
+  if (!h) return set_error(JACOBI_EINVAL, "null handle");
+  if (h->local_halo == (on != 0)) return JACOBI_OK;
+  h->local_halo = on != 0;
+  const Plan& P = h->plan;
+  const int64_t nb = (int64_t)P.blocks.size();
+  std::vector<BlockDev> bd(nb);
+  std::vector<BlockGeom> geo(nb);
+  fill_block_tables(P, h->ws, 0, -1, bd.data(), geo.data(), nullptr, h->local_halo);
+  JGB_CUDA(cudaDeviceSynchronize());  // no launch may be reading the old table
+  // (captured graphs keep working: their launches read the table in device memory)
+  JGB_CUDA(cudaMemcpy(h->d_blocks, bd.data(), nb * sizeof(BlockDev), cudaMemcpyHostToDevice));
   return JACOBI_OK;
 }
 

@@ -12,6 +12,14 @@
 // the role of the tag counters: message n of a direction always uses slot
 // parity n & 1 and sequence number n + 1, so messages match in order and
 // exactly once.
+//
+// A receive posted before its send (in host program order) with a
+// destination buffer is the Channel API's expected message: the receive only
+// registers the buffer, and the matching send copies the payload straight
+// into it in one launch, without the slot.  A zero-copy receive leaves the
+// message in its slot and holds the slot until the next receive at that
+// endpoint or channel_release, so the sender cannot overwrite it while the
+// receiver still reads it.
 #include <cstdlib>
 #include <cstring>
 #include <deque>
@@ -53,6 +61,13 @@ struct channel_s {
   uint64_t sent[2] = {0, 0};   // device-channel messages sent BY endpoint e
   uint64_t recvd[2] = {0, 0};  // device-channel messages received BY endpoint e
                                // (the host-staged and Messaging forms keep out of these)
+  bool held[2] = {false, false};  // endpoint e holds its last message in the slot (zero-copy)
+  struct Posted {                 // receive posted before its send: payload goes straight to dst
+    uint64_t n;
+    void* dst;
+    size_t bytes;
+  };
+  std::deque<Posted> posted[2];   // per receiving endpoint, in message order
   void* hstage[2] = {nullptr, nullptr};  // pinned host staging of the host-staged form, per receiver
   std::deque<MsgMeta> mailbox[2];        // metadata messages waiting at endpoint e
   uint64_t msg_seq[2] = {0, 0};
@@ -98,11 +113,42 @@ __global__ void k_chan_send(ChanCtr* c, int to, uint32_t n, const void* src, voi
   }
 }
 
-// Receive message n at endpoint `at` (dst may be null: zero-copy).
+// Send message n straight into the receiver's pre-posted buffer: wait until
+// every earlier message to that endpoint has been consumed (so "consumed"
+// stays in order), copy, then publish the message as delivered and consumed
+// (it never occupies a slot).
+__global__ void k_chan_send_direct(ChanCtr* c, int to, uint32_t n, const void* src, void* dst, size_t bytes,
+                                   uint64_t wait_ns) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) ok = (n < 1) ? 1 : (wait_seq_ge(&c->consumed[to], n, &c->err, wait_ns) ? 1 : 0);
+  __syncthreads();
+  if (!ok) return;
+  copy16(dst, src, bytes, (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const uint32_t prev = atomicAdd(&c->done[to], 1u);
+    if (prev == gridDim.x - 1) {
+      c->done[to] = 0;
+      c->size[to][n & 1] = bytes;
+      __threadfence();
+      st_release_u32(&c->delivered[to], n + 1);
+      st_release_u32(&c->consumed[to], n + 1);
+    }
+  }
+}
+
+// Release a slot held by a zero-copy receive: consumed[at] = value.
+__global__ void k_chan_release(ChanCtr* c, int at, uint32_t value) { st_release_u32(&c->consumed[at], value); }
+
+// Receive message n at endpoint `at` (dst may be null: zero-copy).  release
+// > 0 first publishes consumed = release for the message this endpoint held;
+// with hold set the message stays in its slot (consumed is not published).
 __global__ void k_chan_recv(ChanCtr* c, int at, uint32_t n, void* dst, const void* slot, size_t bytes,
-                            uint64_t wait_ns, uint32_t* done_ctr) {
+                            uint64_t wait_ns, uint32_t* done_ctr, uint32_t release, int hold) {
   __shared__ int ok;
   if (threadIdx.x == 0) {
+    if (release && blockIdx.x == 0) st_release_u32(&c->consumed[at], release);
     int good = wait_seq_ge(&c->delivered[at], n + 1, &c->err, wait_ns) ? 1 : 0;
     if (good && c->size[at][n & 1] != bytes) {
       atomicCAS(&c->err, (uint32_t)DEV_OK, (uint32_t)DEV_SEQ);
@@ -120,7 +166,7 @@ __global__ void k_chan_recv(ChanCtr* c, int at, uint32_t n, void* dst, const voi
     if (prev == gridDim.x - 1) {
       *done_ctr = 0;
       __threadfence();
-      st_release_u32(&c->consumed[at], n + 1);
+      if (!hold) st_release_u32(&c->consumed[at], n + 1);
     }
   }
 }
@@ -278,9 +324,20 @@ int channel_send(channel_t* ch, int64_t from_block, const void* src, size_t byte
   if ((uintptr_t)src % 16) return set_error(JACOBI_EINVAL, "src must be 16-byte aligned");
   const int to = 1 - from;
   const uint32_t n = (uint32_t)ch->sent[from];
-  k_chan_send<<<copy_ctas(bytes), kChanThreads, 0, S(stream)>>>(ch->ctr, to, n, src, ch->slot[to][n & 1], bytes,
-                                                                  ch->h->wait_ns);
-  JGB_CUDA(cudaGetLastError());
+  if (!ch->posted[to].empty() && ch->posted[to].front().n == ch->sent[from]) {
+    const channel_s::Posted pr = ch->posted[to].front();
+    if (pr.bytes != bytes)
+      return set_error(JACOBI_ESEQ, "channel %u: message %llu has %zu bytes, the posted receive expects %zu", ch->id,
+                       (unsigned long long)pr.n, bytes, pr.bytes);
+    k_chan_send_direct<<<copy_ctas(bytes), kChanThreads, 0, S(stream)>>>(ch->ctr, to, n, src, pr.dst, bytes,
+                                                                         ch->h->wait_ns);
+    JGB_CUDA(cudaGetLastError());
+    ch->posted[to].pop_front();
+  } else {
+    k_chan_send<<<copy_ctas(bytes), kChanThreads, 0, S(stream)>>>(ch->ctr, to, n, src, ch->slot[to][n & 1], bytes,
+                                                                    ch->h->wait_ns);
+    JGB_CUDA(cudaGetLastError());
+  }
   ch->sent[from] += 1;
   return JACOBI_OK;
 }
@@ -292,11 +349,33 @@ int channel_recv(channel_t* ch, int64_t at_block, void* dst, size_t bytes, void*
   if (bytes > ch->max_bytes) return set_error(JACOBI_EINVAL, "message of %zu bytes exceeds max_bytes", bytes);
   if (dst && (uintptr_t)dst % 16) return set_error(JACOBI_EINVAL, "dst must be 16-byte aligned");
   const uint32_t n = (uint32_t)ch->recvd[at];
-  const int ctas = dst ? copy_ctas(bytes) : 1;
-  k_chan_recv<<<ctas, kChanThreads, 0, S(stream)>>>(ch->ctr, at, n, dst, ch->slot[at][n & 1], bytes, ch->h->wait_ns,
-                                                    &ch->ctr->rdone[at]);
-  JGB_CUDA(cudaGetLastError());
+  const uint32_t release = ch->held[at] ? n : 0u;  // the held message is n - 1: consumed = n
+  if (dst && ch->recvd[at] >= ch->sent[1 - at]) {
+    // posted before its send: the send will deliver straight into dst
+    if (release) {
+      k_chan_release<<<1, 1, 0, S(stream)>>>(ch->ctr, at, release);
+      JGB_CUDA(cudaGetLastError());
+    }
+    ch->posted[at].push_back(channel_s::Posted{ch->recvd[at], dst, bytes});
+  } else {
+    const int ctas = dst ? copy_ctas(bytes) : 1;
+    k_chan_recv<<<ctas, kChanThreads, 0, S(stream)>>>(ch->ctr, at, n, dst, ch->slot[at][n & 1], bytes,
+                                                      ch->h->wait_ns, &ch->ctr->rdone[at], release, dst ? 0 : 1);
+    JGB_CUDA(cudaGetLastError());
+  }
+  ch->held[at] = dst == nullptr;
   ch->recvd[at] += 1;
+  return JACOBI_OK;
+}
+
+int channel_release(channel_t* ch, int64_t at_block, void* stream) {
+  if (!ch) return set_error(JACOBI_EINVAL, "null channel");
+  const int at = endpoint_of(ch, at_block);
+  if (at < 0) return set_error(JACOBI_EINVAL, "block %lld is not an endpoint of channel %u", (long long)at_block, ch->id);
+  if (!ch->held[at]) return JACOBI_OK;
+  k_chan_release<<<1, 1, 0, S(stream)>>>(ch->ctr, at, (uint32_t)ch->recvd[at]);
+  JGB_CUDA(cudaGetLastError());
+  ch->held[at] = false;
   return JACOBI_OK;
 }
 
@@ -313,7 +392,13 @@ int channel_sync(channel_t* ch, void* stream) {
   JGB_CUDA(cudaStreamSynchronize(S(stream)));
   JGB_CUDA(cudaMemcpy(ch->h_err, &ch->ctr->err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
   const uint32_t e = *ch->h_err;
-  if (e == DEV_OK) return JACOBI_OK;
+  if (e == DEV_OK) {
+    for (int at = 0; at < 2; ++at)
+      if (!ch->posted[at].empty())
+        return set_error(JACOBI_EAGAIN, "channel %u: a receive posted at block %lld still waits for its send", ch->id,
+                         (long long)ch->block[at]);
+    return JACOBI_OK;
+  }
   JGB_CUDA(cudaMemset(&ch->ctr->err, 0, sizeof(uint32_t)));
   if (e == DEV_TIMEOUT) return set_error(JACOBI_ETIMEDOUT, "channel %u: a device-side wait timed out", ch->id);
   return set_error(JACOBI_ESEQ, "channel %u: message size or sequence mismatch", ch->id);

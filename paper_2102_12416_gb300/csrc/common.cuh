@@ -133,7 +133,80 @@ constexpr uint32_t kEmuHiLimit = 0x7F800000u;
 
 template <typename T> struct C6;
 template <> struct C6<double> { static constexpr double v = 1.0 / 6.0; };
-template <> struct C6<float> { static constexpr float v = 1.0f / 6.0f; };
+
+// ---- the last operation of an update: FP64 s * RN(1/6), FP32 RN(s / 6) -----
+// In FP64 the double nearest 1/6 is 2^-55 relative away from it, far below the
+// iteration's rounding noise.  In FP32 the float nearest 1/6 exceeds it by a
+// third of an ulp, which would scale every update by 1 + 2^-25 and let the
+// iterate drift; FP32 therefore divides, rounding s / 6 once.
+//
+// RN(s / 6) in two operations, by the method of Brisebarre, Muller and Raina
+// for division by a constant known in advance ("Accelerating correctly
+// rounded floating-point division when the divisor is known in advance",
+// IEEE Trans. Computers 53(8), 2004): with zh = RN(1/6) and zl = RN(1/6 - zh),
+// q = RN(s * zh + RN(s * zl)), one multiply and one fused multiply-add.
+// Checked exhaustively over all 2^32 binary32 inputs against IEEE division:
+// equal for +0 and for every finite s with exponent field >= 6
+// (|s| >= 2^-121).  Below that s * zl loses bits to underflow, and -0 and
+// the infinities come out with the wrong sign or as a NaN; div6_small covers
+// those inputs exactly without a division (a Jacobi run from a zero interior
+// carries a band of such tiny values behind its front for thousands of
+// iterations, so this path must stay cheap).  jacobi_selftest_div6 repeats
+// the exhaustive check on the device against the division instruction.
+__device__ __forceinline__ float div6_fast(float s) {
+  constexpr float zh = 0x1.555556p-3f;    // RN(1/6)
+  constexpr float zl = -0x1.555556p-28f;  // RN(1/6 - zh)
+  return __fmaf_rn(s, zh, __fmul_rn(s, zl));
+}
+// True when div6_fast(s) == RN(s / 6): +0, or a finite s with exponent field >= 6.
+__device__ __forceinline__ bool div6_fast_ok(float s) {
+  const uint32_t b = __float_as_uint(s);
+  return ((b & 0x7FFFFFFFu) - 0x03000000u) < (0x7F800000u - 0x03000000u) || b == 0u;
+}
+// RN(s / 6) for the inputs div6_fast does not take:
+//  - infinities and NaNs: s * RN(1/6) keeps both classes (inf / 6 = inf);
+//  - exponent field 4 or 5: s * 2^24 lies in div6_fast's domain and the
+//    quotient is at least 2^-126 (normal), so both scalings are exact;
+//  - exponent field <= 3 (zeros included): s = S * 2^-149 with an integer
+//    S < 2^26, and s / 6 < 2^-124 lies where floats are the multiples of
+//    2^-149 (exponent field 0 or 1, whose encodings are exactly the integers
+//    Q of Q * 2^-149), so RN(s / 6) = RN(S / 6) * 2^-149 with the integer
+//    quotient rounded half to even, and the sign bit copied.
+__device__ __forceinline__ float div6_small(float s) {
+  const uint32_t b = __float_as_uint(s), sign = b & 0x80000000u, a = b ^ sign;
+  if (a >= 0x7F800000u) return __fmul_rn(s, 0x1.555556p-3f);
+  if (a >= 0x02000000u) return __fmul_rn(div6_fast(__fmul_rn(s, 0x1p24f)), 0x1p-24f);
+  const uint32_t e = a >> 23;
+  const uint32_t S = e ? ((a & 0x7FFFFFu) | 0x800000u) << (e - 1u) : a;
+  const uint32_t q0 = S / 6u, r = S - 6u * q0;
+  const uint32_t q = q0 + ((r > 3u) | ((r == 3u) & (q0 & 1u)));
+  return __uint_as_float(q | sign);
+}
+__device__ __forceinline__ float div6(float s) { return div6_fast_ok(s) ? div6_fast(s) : div6_small(s); }
+
+// Finish the updates of N points from their neighbour sums.  FP32: one branch
+// for the whole vector, taken only when some sum lies outside div6_fast's
+// domain.
+template <int N>
+__device__ __forceinline__ void finish_vec(const double (&s)[N], double (&v)[N]) {
+#pragma unroll
+  for (int q = 0; q < N; ++q) v[q] = __dmul_rn(s[q], C6<double>::v);
+}
+template <int N>
+__device__ __forceinline__ void finish_vec(const float (&s)[N], float (&v)[N]) {
+  bool ok = true;
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    v[q] = div6_fast(s[q]);
+    ok = ok && div6_fast_ok(s[q]);
+  }
+  if (!ok) {
+#pragma unroll
+    for (int q = 0; q < N; ++q) v[q] = div6(s[q]);
+  }
+}
+__device__ __forceinline__ double finish1(double s) { return __dmul_rn(s, C6<double>::v); }
+__device__ __forceinline__ float finish1(float s) { return div6(s); }
 
 // ---- SplitMix64 (Steele, Lea, Flood 2014) as a counter-based generator -------
 // n-th output (0-based) of the stream seeded with `seed`.

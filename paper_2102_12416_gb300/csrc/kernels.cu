@@ -248,6 +248,21 @@ __global__ void k_selftest_widen(unsigned long long* bad) {
   if (n) atomicAdd(bad, n);
 }
 
+// Every binary32 bit pattern through div6 (the FP32 update's RN(s / 6) in two
+// operations, with its fallback), against the division instruction sequence:
+// counts results that differ bit for bit (a NaN must stay a NaN).
+__global__ void k_selftest_div6(unsigned long long* bad) {
+  unsigned long long n = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < (1ull << 32); x += stride) {
+    const float f = __uint_as_float((uint32_t)x);
+    const float a = div6(f), b = __fdiv_rn(f, 6.0f);
+    const bool ok = (a != a && b != b) || __float_as_uint(a) == __float_as_uint(b);
+    n += ok ? 0ull : 1ull;
+  }
+  if (n) atomicAdd(bad, n);
+}
+
 // Pipe-rate probe: chains of FP64 adds on the FP64 pipe (EMU = false) or
 // through dadd_nn on the integer pipe (EMU = true); 8 independent chains per
 // thread keep either pipe busy.  The result is stored so nothing is elided.
@@ -288,16 +303,17 @@ __global__ void k_reduce(const GridDev* grids, GridNorm* norms, const int32_t* g
 }
 
 // Explicit exchange, step 1: pack each internal face of the new iterate
-// (parity p ^ 1 state) into a contiguous staging buffer.
+// (parity p ^ 1 state) into a contiguous staging buffer, or (direct) straight
+// into the neighbour's receive slot for the next parity.
 template <typename T>
-__global__ void k_pack_faces(const BlockDev* __restrict__ blocks, void* const* staging, const GridDev* grids,
-                             int64_t it) {
-  const int b = blockIdx.x, f = blockIdx.y;
+__global__ void k_pack_faces(const BlockDev* __restrict__ blocks, const int32_t* __restrict__ ids,
+                             void* const* staging, const GridDev* grids, int64_t it, int direct) {
+  const int b = ids[blockIdx.x], f = blockIdx.y;
   const BlockDev& B = blocks[b];
   if (B.nbr[f] < 0) return;
   const int p = (int)((it - grids[B.grid].start_iter) & 1);
   const T* U = (const T*)B.u[p ^ 1];
-  T* S = (T*)staging[b * 6 + f];
+  T* S = direct ? (T*)B.send[f][p ^ 1] : (T*)staging[b * 6 + f];
   const int64_t nx = B.nx, ny = B.ny, nz = B.nz, rx = B.rx, ry = B.ry;
   const int64_t n = face_elems(B, f);
   for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {  // padding entries copy padding
@@ -312,9 +328,9 @@ __global__ void k_pack_faces(const BlockDev* __restrict__ blocks, void* const* s
 // Explicit exchange, step 2: the channel transfer of each packed face into the
 // neighbour's receive slot for the next parity.
 template <typename T>
-__global__ void k_copy_faces(const BlockDev* __restrict__ blocks, void* const* staging, const GridDev* grids,
-                             int64_t it) {
-  const int b = blockIdx.x, f = blockIdx.y;
+__global__ void k_copy_faces(const BlockDev* __restrict__ blocks, const int32_t* __restrict__ ids,
+                             void* const* staging, const GridDev* grids, int64_t it) {
+  const int b = ids[blockIdx.x], f = blockIdx.y;
   const BlockDev& B = blocks[b];
   if (B.nbr[f] < 0) return;
   const int p = (int)((it - grids[B.grid].start_iter) & 1);
@@ -324,7 +340,23 @@ __global__ void k_copy_faces(const BlockDev* __restrict__ blocks, void* const* s
   for (int64_t e = threadIdx.x; e < n; e += blockDim.x) D[e] = S[e];
 }
 
+// Posted receives of the GPU Messaging form: one CTA per descriptor copies
+// its payload (16-byte vectors; every face buffer is a whole number of them).
+__global__ void k_copy_desc(const CopyDesc* __restrict__ d, int32_t n) {
+  const CopyDesc c = d[blockIdx.x];
+  const uint4* src = (const uint4*)c.src;
+  uint4* dst = (uint4*)c.dst;
+  const int64_t nv = c.bytes / 16;
+  for (int64_t q = threadIdx.x; q < nv; q += blockDim.x) dst[q] = __ldcg(src + q);
+}
+
 }  // namespace
+
+cudaError_t launch_copy_desc(const CopyDesc* d, int32_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_copy_desc<<<n, 256, 0, s>>>(d, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_bnorm(const StepLaunch& a, cudaStream_t s) {
   if (a.n_items <= 0) return cudaSuccess;
@@ -340,21 +372,21 @@ cudaError_t launch_reduce(const GridDev* grids, GridNorm* norms, const int32_t* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_faces(const BlockDev* blocks, int32_t n_blocks, void* const* staging, const GridDev* grids,
-                              int64_t it, int32_t dtype, cudaStream_t s) {
+cudaError_t launch_pack_faces(const BlockDev* blocks, const int32_t* ids, int32_t n_blocks, void* const* staging,
+                              const GridDev* grids, int64_t it, int32_t dtype, cudaStream_t s, bool direct) {
   if (n_blocks <= 0) return cudaSuccess;
   const dim3 grid(n_blocks, 6);
-  if (dtype == 0) k_pack_faces<double><<<grid, 256, 0, s>>>(blocks, staging, grids, it);
-  else k_pack_faces<float><<<grid, 256, 0, s>>>(blocks, staging, grids, it);
+  if (dtype == 0) k_pack_faces<double><<<grid, 256, 0, s>>>(blocks, ids, staging, grids, it, direct ? 1 : 0);
+  else k_pack_faces<float><<<grid, 256, 0, s>>>(blocks, ids, staging, grids, it, direct ? 1 : 0);
   return cudaGetLastError();
 }
 
-cudaError_t launch_copy_faces(const BlockDev* blocks, int32_t n_blocks, void* const* staging, const GridDev* grids,
-                              int64_t it, int32_t dtype, cudaStream_t s) {
+cudaError_t launch_copy_faces(const BlockDev* blocks, const int32_t* ids, int32_t n_blocks, void* const* staging,
+                              const GridDev* grids, int64_t it, int32_t dtype, cudaStream_t s) {
   if (n_blocks <= 0) return cudaSuccess;
   const dim3 grid(n_blocks, 6);
-  if (dtype == 0) k_copy_faces<double><<<grid, 256, 0, s>>>(blocks, staging, grids, it);
-  else k_copy_faces<float><<<grid, 256, 0, s>>>(blocks, staging, grids, it);
+  if (dtype == 0) k_copy_faces<double><<<grid, 256, 0, s>>>(blocks, ids, staging, grids, it);
+  else k_copy_faces<float><<<grid, 256, 0, s>>>(blocks, ids, staging, grids, it);
   return cudaGetLastError();
 }
 
@@ -379,6 +411,11 @@ cudaError_t launch_selftest_dadd(const double* a, const double* b, int64_t n, do
 
 cudaError_t launch_selftest_widen(unsigned long long* bad, cudaStream_t s) {
   k_selftest_widen<<<1216, 256, 0, s>>>(bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_selftest_div6(unsigned long long* bad, cudaStream_t s) {
+  k_selftest_div6<<<1216, 256, 0, s>>>(bad);
   return cudaGetLastError();
 }
 

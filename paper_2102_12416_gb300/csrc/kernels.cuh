@@ -82,12 +82,24 @@ enum StepMode : int { kWrite = 1, kPack = 2, kResid = 4 };
 // kinds run concurrently; without it they run one after another on s.
 cudaError_t launch_step(const StepLaunch& a, int mode, cudaStream_t s, const KindFork* fork = nullptr);
 
-// Explicit exchange: pack every internal face of the NEW iterate into its
-// staging buffer, then copy staging buffers into the neighbours' slots.
-cudaError_t launch_pack_faces(const BlockDev* blocks, int32_t n_blocks, void* const* staging,
+// Explicit exchange over the blocks ids[0..n_blocks): pack every internal
+// face of the NEW iterate into its staging buffer (direct: straight into the
+// neighbour's receive slot), or copy staging buffers into the neighbours'
+// slots.
+cudaError_t launch_pack_faces(const BlockDev* blocks, const int32_t* ids, int32_t n_blocks, void* const* staging,
+                              const GridDev* grids, int64_t it, int32_t dtype, cudaStream_t s,
+                              bool direct = false);
+cudaError_t launch_copy_faces(const BlockDev* blocks, const int32_t* ids, int32_t n_blocks, void* const* staging,
                               const GridDev* grids, int64_t it, int32_t dtype, cudaStream_t s);
-cudaError_t launch_copy_faces(const BlockDev* blocks, int32_t n_blocks, void* const* staging,
-                              const GridDev* grids, int64_t it, int32_t dtype, cudaStream_t s);
+
+// One posted receive of the GPU Messaging form: copy `bytes` (a multiple of
+// 16, both addresses 16-byte aligned) from src to dst.
+struct CopyDesc {
+  const void* src;
+  void* dst;
+  int64_t bytes;
+};
+cudaError_t launch_copy_desc(const CopyDesc* d, int32_t n, cudaStream_t s);
 
 // Domain check of the integer-pipe FP64 adder (sets GridNorm::emu_bad) and
 // its self-test.
@@ -95,6 +107,7 @@ cudaError_t launch_emu_check(const BlockDev* blocks, int32_t n_blocks, const Gri
                              const int32_t* grid_ids, int32_t n_grids, int64_t it, cudaStream_t s);
 cudaError_t launch_selftest_dadd(const double* a, const double* b, int64_t n, double* out, cudaStream_t s);
 cudaError_t launch_selftest_widen(unsigned long long* bad, cudaStream_t s);
+cudaError_t launch_selftest_div6(unsigned long long* bad, cudaStream_t s);
 cudaError_t launch_pipe_rate(bool emu, int blocks, int threads, int iters, double* out, cudaStream_t s);
 
 // |b|^2 partials (interior = 0, only Dirichlet ghosts).

@@ -1,13 +1,13 @@
 // Allocation-free residual of a caller-owned padded state array.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// residual: code running while a CUDA stream is being captured into a graph
-// (cudaMalloc is not a stream operation and would break or be refused by the
-// capture), and applications that reserve all device memory up front and
-// forbid later allocations (fixed-footprint services, or frameworks whose
-// caching allocator must see every allocation).  For them this file keeps the
-// reduction scratch in a fixed file-scope device array instead of a
-// workspace: every GPU that loads the library holds it (256 KB) until exit.
+// residual: services that reserve all device memory up front and forbid
+// later allocations (a fixed footprint, or a framework whose caching
+// allocator must account for every byte), and loops that cannot afford the
+// device-wide synchronisation a cudaMalloc or cudaFree may bring.  For them
+// this file keeps the reduction scratch in a fixed file-scope device array
+// instead of a workspace: every GPU that loads the library holds it (256 KB)
+// until exit.
 //
 // The array is shared by every call on a device and keeps the last call's
 // contents; each call overwrites every partial it later reads, so nothing has

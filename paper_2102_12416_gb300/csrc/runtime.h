@@ -65,7 +65,10 @@ struct Plan {
   int64_t n_units = 0;     // persistent-kernel units: (block, z-chunk) pairs
   // byte offsets into the workspace
   size_t off_blocks, off_geom, off_items, off_active, off_kind, off_grids, off_norms, off_inits, off_gids, off_partials,
-      off_progress, off_err, off_stage_tab, off_punit_items, off_punit_ids, off_pdep_off, off_pdep_ids;
+      off_progress, off_err, off_stage_tab, off_punit_items, off_punit_ids, off_pdep_off, off_pdep_ids,
+      off_active_blocks;
+  size_t off_stage_begin = 0, off_stage_end = 0;  // the explicit-path staging buffers, contiguous
+  int64_t halo_faces = 0;                         // internal faces (one message each per iteration)
   size_t bytes = 0;
 };
 
@@ -85,9 +88,10 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
 // Device block table entries of a plan whose workspace starts at `ws`; block
 // and neighbour ids are offset by `base`; grid_override >= 0 replaces every
 // block's grid index.  stage_tab (nullable) receives the explicit-path staging
-// buffers (6 per block).
+// buffers (6 per block).  local_halo aims every block's face stores at its own
+// receive slots instead of its neighbours' (the halo-share measurement).
 void fill_block_tables(const Plan& P, char* ws, int64_t base, int32_t grid_override, BlockDev* bd, BlockGeom* geo,
-                       void** stage_tab);
+                       void** stage_tab, bool local_halo = false);
 
 }  // namespace jgb
 
@@ -119,6 +123,7 @@ struct jacobi_s {
   int32_t* d_punit_ids = nullptr;
   int32_t* d_pdep_off = nullptr;
   int32_t* d_pdep_ids = nullptr;
+  int32_t* d_active_blocks = nullptr;  // blocks of the active grids (exchange kernels)
 
   // host mirrors
   std::vector<jgb::WorkItem> active_items;
@@ -129,6 +134,7 @@ struct jacobi_s {
   std::vector<int32_t> active_dep_off;      // n_active_units + 1 offsets into active_deps
   std::vector<int32_t> active_deps;
   std::vector<int32_t> active_grids;
+  std::vector<int32_t> active_blocks;
   std::vector<jgb::WorkItem> kind_items;        // active items grouped by kind
   int32_t kind_off[jgb::kItemKinds + 1] = {};
   bool tables_dirty = true;
@@ -146,7 +152,18 @@ struct jacobi_s {
   int32_t stages = 4;             // ring stages of the plane-streaming path
   int32_t fp64_emu = 1;           // FP64 pair sums on the integer pipe when safe
   int64_t drop_block = -1;        // fault injection (persistent path)
+  bool local_halo = false;        // halo-share measurement: face stores stay in the block
   void* stage = nullptr;          // device staging for host transfers
   size_t stage_bytes = 0;
+  // host-driven exchange forms (CHANNEL, MESSAGING, HOST_STAGED paths)
+  void* h_halo = nullptr;                       // pinned copy of the staging region (HOST_STAGED)
+  jgb::CopyDesc* d_desc = nullptr;              // posted receives of one exchange (MESSAGING)
+  jgb::CopyDesc* h_desc = nullptr;              // pinned
+  struct HaloMeta {                             // metadata message of one face (MESSAGING)
+    const void* src;
+    int64_t bytes;
+    int32_t face;                               // the receiver's face the payload belongs to
+  };
+  std::vector<std::vector<HaloMeta>> mailbox;   // per receiving block
   std::vector<channel_s*> channels;
 };

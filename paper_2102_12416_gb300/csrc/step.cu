@@ -5,9 +5,10 @@
 // the neighbours' receive slots, the intra-device form of the Channel API of
 // Sec. 3.2.2) and the FP64 residual fused in on check iterations.
 //
-// Stencil reading: u' = (((xm + xp) + (ym + yp)) + (zm + zp)) * c6, c6 = 1/6
-// rounded to the state type, every operation rounded on its own (no FMA), so
-// FP64 results are bit-exact with a monolithic CPU evaluation in that order.
+// Stencil reading: s = ((xm + xp) + (ym + yp)) + (zm + zp), then u' = s * c6
+// in FP64 (c6 = 1/6 rounded to double) and u' = RN(s / 6) in FP32, every
+// operation rounded on its own (no contraction of the sum), so results are
+// bit-exact with a monolithic CPU evaluation in that order.
 //
 // Two ways to sweep a work item:
 //  * plane streaming (x0 < 0): the CTA owns whole x-y planes of one block over
@@ -159,7 +160,7 @@ __device__ __forceinline__ double tile_sweep(const BlockDev& B, int p, int x0, i
     const T yp = (j < ny - 1) ? U[o + rx] : __ldcg(ryp + (int64_t)k * rx + i);
     const T s = radd(radd(radd(xm, xp), radd(ym, yp)), radd(below, above));
     if (MODE & kWrite) {
-      const T v = rmul(s, C6<T>::v);
+      const T v = finish1(s);
       V[o] = v;
       if (MODE & kPack) {
         if (sxm) sxm[(int64_t)k * ry + j] = v;
@@ -371,7 +372,7 @@ __device__ __forceinline__ double stream_plane(const PlaneView<T>& O, int k, int
       left = i0 > 0 ? Pc[j * rx + i0 - 1] : Gxm[j];
       right = i0 + VEC < nx ? Pc[j * rx + i0 + VEC] : Gxp[j];
     }
-    T v[VEC];
+    T v[VEC], sv[VEC];
 #pragma unroll
     for (int q = 0; q < VEC; ++q) {
       const T xm = q == 0 ? left : c[r][q > 0 ? q - 1 : 0];
@@ -381,12 +382,17 @@ __device__ __forceinline__ double stream_plane(const PlaneView<T>& O, int k, int
       // 64^3 blocks, +1.9 % on 32^3; 3 or 4 of 8 gained less).
       const T s = (q == VEC - 1 && r < 2) ? nsum_zn<T, EMU>(xm, xp, ym[q], yp[q], zm[q], zp[q])
                                           : nsum<T, EMU>(xm, xp, ym[q], yp[q], zm[q], zp[q]);
-      v[q] = rmul(s, C6<T>::v);
+      // FP64 finishes each point at once (keeping the sum live to the end of
+      // the loop made ptxas spill); FP32 finishes the vector after the loop
+      // (one fallback branch per vector).
+      if constexpr (sizeof(T) == 8) v[q] = finish1(s);
+      else sv[q] = s;
       if (MODE & kResid) {
         const double e2 = resid2<T>(xm, xp, ym[q], yp[q], zm[q], zp[q], s, c[r][q]);
         acc += (!RAG || (q <= ql && j < ny)) ? e2 : 0.0;
       }
     }
+    if constexpr (sizeof(T) == 4) finish_vec(sv, v);
     if ((MODE & kWrite) && (MODE & kPack)) {
       T last = v[VEC - 1];
       if (RAG) {

@@ -1,10 +1,16 @@
 """Channel semantics on the GPU (Sec. 3.2.2 Channel API, Sec. 3.1 tag counters).
 
 * payload delivered = payload sent, bit for bit, message by message, in order;
-* zero-copy receives leave message n in the slot of parity n & 1;
+* a receive posted before its send gets the payload straight into its buffer
+  (the slot stays untouched), mixed in any order with slot-path and zero-copy
+  messages;
+* zero-copy receives leave message n in the slot of parity n & 1 and hold the
+  slot until the next receive or channel_release: a send that would overwrite
+  it waits (bounded) instead;
 * a size mismatch is reported as JACOBI_ESEQ;
-* a receive with no matching send times out (bounded wait) with
-  JACOBI_ETIMEDOUT instead of hanging, and the context stays usable;
+* a waiting receive with no matching send times out (bounded wait) with
+  JACOBI_ETIMEDOUT instead of hanging, and the context stays usable; a posted
+  receive still waiting for its send is reported as JACOBI_EAGAIN;
 * the on-device ping-pong completes for 8 B .. 4 MB and leaves the payload.
 """
 import pytest
@@ -119,14 +125,98 @@ def test_size_mismatch_is_seq_error(solver):
 def test_recv_without_send_times_out(solver):
     ch = jg.channel_open(solver.h, 11, 0, 7, 256)
     try:
-        d = torch.zeros(256, dtype=torch.uint8, device="cuda")
-        jg.channel_recv(ch, 7, d.data_ptr(), 256)  # nothing was sent
+        jg.channel_recv(ch, 7, None, 256)  # zero-copy: waits on the device; nothing was sent
         with pytest.raises(jg.JacobiError) as e:
             jg.channel_sync(ch)
         assert e.value.code == jg.JACOBI_ETIMEDOUT
     finally:
         jg.channel_close(ch)
     # the GPU context is still usable afterwards
+    solver.step(2)
+    solver.sync()
+
+
+def test_posted_receive_gets_payload_directly(solver):
+    n = 4096
+    ch = jg.channel_open(solver.h, 13, 0, 1, n)
+    try:
+        dst = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        jg.channel_recv(ch, 1, dst.data_ptr(), n)  # posted before the send
+        with pytest.raises(jg.JacobiError) as e:
+            jg.channel_sync(ch)
+        assert e.value.code == jg.JACOBI_EAGAIN
+        m = _payload(n, 40)
+        jg.channel_send(ch, 0, m.data_ptr(), n)
+        jg.channel_sync(ch)
+        assert torch.equal(dst, m)
+        # the message went straight to dst: the slot of its parity is untouched
+        assert int(_view(jg.channel_slot(ch, 1, 0), n).sum()) == 0
+        # posted, slot path, zero-copy and posted again, both directions
+        outs = []
+        for k in range(8):
+            m = _payload(n, 41 + k)
+            d = torch.zeros(n, dtype=torch.uint8, device="cuda")
+            a, b = (0, 1) if k % 2 == 0 else (1, 0)
+            mode = k % 3
+            if mode == 0:
+                jg.channel_recv(ch, b, d.data_ptr(), n)
+                jg.channel_send(ch, a, m.data_ptr(), n)
+            elif mode == 1:
+                jg.channel_send(ch, a, m.data_ptr(), n)
+                jg.channel_recv(ch, b, d.data_ptr(), n)
+            else:
+                jg.channel_send(ch, a, m.data_ptr(), n)
+                jg.channel_recv(ch, b, None, n)
+                parity = sum(1 for j in range(k) if (j % 2 == 0) == (k % 2 == 0)) + (1 if b == 1 else 0)
+                jg.channel_sync(ch)
+                d.copy_(_view(jg.channel_slot(ch, b, parity & 1), n))
+                jg.channel_release(ch, b)
+            jg.channel_sync(ch)
+            outs.append((d, m))
+        for k, (d, m) in enumerate(outs):
+            assert torch.equal(d, m), k
+        # a posted receive of another size: the send is refused at once
+        d = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        jg.channel_recv(ch, 1, d.data_ptr(), 1024)
+        with pytest.raises(jg.JacobiError) as e:
+            jg.channel_send(ch, 0, _payload(512, 3).data_ptr(), 512)
+        assert e.value.code == jg.JACOBI_ESEQ
+    finally:
+        jg.channel_close(ch)
+
+
+def test_zero_copy_holds_slot_until_released(solver):
+    n = 1024
+    msgs = [_payload(n, 60 + k) for k in range(3)]
+    ch = jg.channel_open(solver.h, 14, 2, 3, n)
+    try:
+        jg.channel_send(ch, 2, msgs[0].data_ptr(), n)
+        jg.channel_recv(ch, 3, None, n)  # message 0 stays in slot 0, held
+        jg.channel_send(ch, 2, msgs[1].data_ptr(), n)  # slot 1: free
+        jg.channel_send(ch, 2, msgs[2].data_ptr(), n)  # slot 0: held, so this send must wait
+        with pytest.raises(jg.JacobiError) as e:
+            jg.channel_sync(ch)
+        assert e.value.code == jg.JACOBI_ETIMEDOUT
+        assert torch.equal(_view(jg.channel_slot(ch, 3, 0), n), msgs[0])
+    finally:
+        jg.channel_close(ch)
+    # released after reading, the same sequence goes through
+    ch = jg.channel_open(solver.h, 15, 2, 3, n)
+    try:
+        jg.channel_send(ch, 2, msgs[0].data_ptr(), n)
+        jg.channel_recv(ch, 3, None, n)
+        got0 = _view(jg.channel_slot(ch, 3, 0), n).clone()
+        jg.channel_release(ch, 3)
+        jg.channel_send(ch, 2, msgs[1].data_ptr(), n)
+        jg.channel_send(ch, 2, msgs[2].data_ptr(), n)
+        d1 = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        d2 = torch.zeros_like(d1)
+        jg.channel_recv(ch, 3, d1.data_ptr(), n)
+        jg.channel_recv(ch, 3, d2.data_ptr(), n)
+        jg.channel_sync(ch)
+        assert torch.equal(got0, msgs[0]) and torch.equal(d1, msgs[1]) and torch.equal(d2, msgs[2])
+    finally:
+        jg.channel_close(ch)
     solver.step(2)
     solver.sync()
 

@@ -4,7 +4,8 @@ exponent field < 2040); numpy's float64 addition is the reference.  And the
 step kernels give identical iterates whether the pair sums run on the integer
 pipe or on the FP64 pipe (JACOBI_FP64_EMU=0).  The FP32 residual's
 integer-pipe widening (binary32 -> binary64) equals the conversion
-instruction on all 2^32 inputs."""
+instruction on all 2^32 inputs, and so does the FP32 update's two-operation
+division by 6 against the division instruction sequence."""
 import numpy as np
 import pytest
 
@@ -93,3 +94,28 @@ def test_negative_values_keep_the_fp64_pipe(oracle_mod):
 def test_widen_f32_exhaustive():
     # every binary32 bit pattern, on the device, bit for bit (NaN stays NaN)
     assert jg.jacobi_selftest_widen() == 0
+
+
+def test_div6_f32_exhaustive():
+    """The FP32 update's RN(s / 6) (one multiply and one fused multiply-add,
+    with the division itself outside that form's proven domain) equals the
+    division instruction sequence on all 2^32 binary32 inputs, bit for bit."""
+    assert jg.jacobi_selftest_div6() == 0
+
+
+def test_fp32_tiny_and_signed_values_divide_exactly(oracle_mod):
+    """FP32 states whose neighbour sums fall outside the two-operation
+    division's domain (|s| < 2^-121, negative zeros) take the exact fallback:
+    iterates still equal the FP32 oracle's RN(s / 6) bit for bit, sign of zero
+    included."""
+    nx, ny, nz = 21, 13, 9
+    u = J.initial_grid(nx, ny, nz, "uniform", bc_seed=13, interior="uniform", interior_seed=14,
+                       dtype=np.float32)
+    u = (u - np.float32(0.5)) * np.float32(2.0 ** -118)  # sums straddle 2^-121 and change sign
+    u[:, :, : nx // 2] = np.float32(-0.0)
+    with jg.Jacobi3D((nx, ny, nz), ("shape", (8, 8, 8)), "f32") as s:
+        s.set_state(u)
+        s.step(3)
+        got = s.copy_out()
+    want = J.interior_of(oracle_mod.jacobi(u, 3))
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))

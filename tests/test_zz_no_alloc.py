@@ -1,14 +1,15 @@
-"""The allocation-free residual entry point, checked against jacobi_residual.
+"""The allocation-free residual entry point, checked against the oracle and
+against jacobi_residual.
 
-jacobi_residual_noalloc exists for callers that may not allocate device
-memory when they need a residual: code running inside a CUDA stream capture
-(an allocation is not a stream operation and breaks the capture) and services
-that reserve all device memory at start-up and forbid later allocations.  It
-keeps its reduction scratch in a fixed array inside the library, so two calls
-in a row must each see only their own data.  The test compares two
-consecutive calls on different states with the handle-based jacobi_residual
-(same tolerance as the other residual parity tests), and checks that a grid
-larger than the fixed scratch is refused.
+jacobi_residual_noalloc is for callers that may not allocate device memory
+when they need a residual: services that reserve all device memory at
+start-up and forbid later allocations, and loops that cannot afford the
+device-wide synchronisation a cudaMalloc or cudaFree may bring.  It keeps its
+reduction scratch in a fixed array inside the library, so two calls in a row
+must each see only their own data.  The test compares two consecutive calls
+on different states with the CPU oracle's residual of the same state and with
+the handle-based jacobi_residual (the tolerance of the other residual parity
+tests), and checks that a grid larger than the fixed scratch is refused.
 """
 import pytest
 
@@ -39,7 +40,7 @@ def _reference(grid, dtype, init, iters):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_noalloc_matches_jacobi_residual_twice(dtype):
+def test_noalloc_matches_oracle_and_jacobi_residual_twice(oracle_mod, dtype):
     cases = [((40, 33, 27), dict(bc="uniform", bc_seed=71, interior="uniform", interior_seed=72), 5),
              ((24, 48, 35), dict(bc="linear_noise", bc_seed=73, noise_amp=1e-3, interior="zero"), 11)]
     out = torch.zeros(3, dtype=torch.float64, device="cuda")
@@ -49,6 +50,9 @@ def test_noalloc_matches_jacobi_residual_twice(dtype):
         jg.jacobi_residual_noalloc(u.data_ptr(), grid, dtype, out.data_ptr())
         torch.cuda.synchronize()
         got_r, got_b, got_rel = (float(v) for v in out.cpu())
+        orn, obn, orel = oracle_mod.residual(state)
+        assert abs(got_r - orn) <= RES_TOL * orn and abs(got_b - obn) <= RES_TOL * obn
+        assert abs(got_rel - orel) <= RES_TOL * orel
         assert abs(got_r - ab) <= RES_TOL * ab
         assert abs(got_rel - rel) <= RES_TOL * rel
         assert abs(got_r / got_b - got_rel) <= 1e-15 * got_rel

@@ -196,6 +196,9 @@ typedef struct {
                             too wide to stream); [1..3] plane streaming with 8,
                             4, 2 consumer warps per CTA; [4..6] the same for
                             blocks with padded (ragged) rows; [7] unused */
+  int64_t zchunk;        /* work-item shape (see jacobi_set_shape): planes per item */
+  int32_t cw_cap;        /*   and the consumer-warp cap of streaming CTAs         */
+  int32_t pad2_;
 } jacobi_info_t;
 
 /* Outcome of jacobi_autotune. */
@@ -205,6 +208,9 @@ typedef struct {
   double ms_per_iter;    /* measured time per iteration of the chosen config    */
   int32_t n_tried;       /* candidates timed (0 when taken from the cache)      */
   int32_t from_cache;
+  int64_t zchunk;        /* chosen z-chunk depth (planes per work item)         */
+  int32_t cw_cap;        /* chosen consumer-warp cap per streaming CTA (2/4/8)  */
+  int32_t pad_;
 } jacobi_tune_result;
 
 /* ---- errors -------------------------------------------------------------- */
@@ -263,14 +269,29 @@ int jacobi_block(const jacobi_t* h, int64_t block, jacobi_block_info* out);
  * there are more. */
 int jacobi_set_path(jacobi_t* h, int32_t path);
 
-/* Autotuner (the library's addition): times every candidate step
- * configuration -- path FUSED/GRAPH, and PERSISTENT x ring depth 3..6 where
- * it fits shared memory -- for iters_per_trial
- * iterations on a scratch handle with the same grids, splits and dtype (the
- * handle's own state is untouched), then applies the fastest to `h`.  All
- * candidates give bit-identical iterates.  When the environment variable
- * JACOBI_TUNE_CACHE names a file, results are looked up there by a signature
- * of the geometry and appended after a search.  Synchronises the stream. */
+/* Work-item shape of the step kernels (the library's addition; the block
+ * split itself is the caller's).  zchunk: planes per work item along z (0 =
+ * the library's cost model; clamped to the tallest block).  cw_cap: at most 2,
+ * 4 or 8 consumer warps per plane-streaming CTA; a CTA of CW warps covers
+ * 4 * 32 * CW / (row vectors) rows of a plane, so a lower cap cuts planes into
+ * more, shorter row windows (a row's vectors always fit one CTA).  Iterates do
+ * not depend on the shape (bit for bit); residual sums are reproducible for a
+ * given shape.  The item tables hold the finest shape down to a quarter of
+ * the planned z-chunk and 2 warps: finer ones give JACOBI_EINVAL.
+ * Synchronises the stream. */
+int jacobi_set_shape(jacobi_t* h, int64_t zchunk, int32_t cw_cap, void* stream);
+
+/* Autotuner (the library's addition): times candidate step configurations
+ * for iters_per_trial iterations on a scratch handle with the same grids,
+ * splits and dtype (the handle's own state is untouched): every shape of
+ * jacobi_set_shape with a z-chunk of 2, 1, 1/2 or 1/4 times the cost model's
+ * and a warp cap of 8, 4 or 2 (shapes that give the same items are timed
+ * once), each on the GRAPH path and the PERSISTENT kernel; then FUSED and the
+ * persistent ring depths 3..6 at the best shape.  Applies the fastest (path,
+ * ring depth, shape) to `h`.  All candidates give bit-identical iterates.
+ * When the environment variable JACOBI_TUNE_CACHE names a file, results are
+ * looked up there by a signature of the geometry and appended after a search.
+ * Synchronises the stream. */
 int jacobi_autotune(jacobi_t* h, int64_t iters_per_trial, void* stream, jacobi_tune_result* out);
 
 /* ---- state transfer ---------------------------------------------------------- */

@@ -70,12 +70,12 @@ class jacobi_info_t(ctypes.Structure):
                 ("iteration", c_int64), ("dtype", c_int32), ("path", c_int32),
                 ("halo_bytes_per_iter", c_int64), ("workspace_bytes", c_size_t), ("stages", c_int32),
                 ("item_kinds", c_int32), ("fp64_int_adds", c_int32), ("pad_", c_int32),
-                ("kind_items", c_int32 * 8)]
+                ("kind_items", c_int32 * 8), ("zchunk", c_int64), ("cw_cap", c_int32), ("pad2_", c_int32)]
 
 
 class jacobi_tune_result(ctypes.Structure):
     _fields_ = [("path", c_int32), ("stages", c_int32), ("ms_per_iter", c_double), ("n_tried", c_int32),
-                ("from_cache", c_int32)]
+                ("from_cache", c_int32), ("zchunk", c_int64), ("cw_cap", c_int32), ("pad_", c_int32)]
 
 
 class serve_config(ctypes.Structure):
@@ -129,6 +129,7 @@ _SIGS = {
     "jacobi_solve": (ctypes.c_int, [P, c_double, c_int64, c_int64, c_int64, P, P, P, P]),
     "jacobi_sync": (ctypes.c_int, [P, P]),
     "jacobi_autotune": (ctypes.c_int, [P, c_int64, P, ctypes.POINTER(jacobi_tune_result)]),
+    "jacobi_set_shape": (ctypes.c_int, [P, c_int64, c_int32, P]),
     "jacobi_read_face": (ctypes.c_int, [P, c_int64, c_int32, P, P]),
     "jacobi_debug_drop_block": (ctypes.c_int, [P, c_int64]),
     "jacobi_measure_local_halo": (ctypes.c_int, [P, c_int32]),
@@ -327,6 +328,10 @@ def jacobi_autotune(h, iters_per_trial, stream=None) -> jacobi_tune_result:
     out = jacobi_tune_result()
     _call("jacobi_autotune", h, iters_per_trial, _stream(stream), ctypes.byref(out))
     return out
+
+
+def jacobi_set_shape(h, zchunk=0, cw_cap=8, stream=None):
+    _call("jacobi_set_shape", h, zchunk, cw_cap, _stream(stream))
 
 
 def jacobi_sync(h, stream=None):
@@ -533,7 +538,10 @@ class Jacobi3D:
     def autotune(self, iters_per_trial=50) -> dict:
         r = jacobi_autotune(self.h, iters_per_trial, self.stream)
         return {"path": PATH_NAMES[r.path], "stages": r.stages, "ms_per_iter": r.ms_per_iter,
-                "n_tried": r.n_tried, "from_cache": bool(r.from_cache)}
+                "n_tried": r.n_tried, "from_cache": bool(r.from_cache), "zchunk": r.zchunk, "cw_cap": r.cw_cap}
+
+    def set_shape(self, zchunk=0, cw_cap=8):
+        jacobi_set_shape(self.h, zchunk, cw_cap, self.stream)
 
     def launch_kinds(self) -> int:
         return max(1, self.info.item_kinds)

@@ -52,11 +52,12 @@ static int axis_split(int64_t n, int32_t mode, int64_t param, std::vector<std::p
 // Consumer warps per CTA for the plane-streaming path, or 0 when a padded
 // row is wider than one CTA can cover (more than 256 vectors of 16 bytes).
 // Each consumer thread computes 4 rows of one vector column; a CTA of CW
-// consumer warps (2, 4 or 8: the smallest that covers the padded plane)
-// covers a window of `chunk` rows (a multiple of 4), so large planes are split
-// into ceil(ry / chunk) windows and small ones run in small CTAs, several per
-// SM.  A ring stage of a window must fit shared memory four times over.
-static int stream_shape(int64_t rx, int64_t ry, size_t elem, uint32_t* stage_bytes, int64_t* chunk) {
+// consumer warps (2, 4 or 8: the smallest that covers the padded plane, at
+// most cw_cap, but never fewer than one row of vector columns needs) covers a
+// window of `chunk` rows (a multiple of 4), so large planes are split into
+// ceil(ry / chunk) windows and small ones run in small CTAs, several per SM.
+// A ring stage of a window must fit shared memory four times over.
+static int stream_shape(int64_t rx, int64_t ry, size_t elem, int cw_cap, uint32_t* stage_bytes, int64_t* chunk) {
   const int64_t txv = rx / (16 / (int64_t)elem);
   if (txv > kThreads) return 0;
   int cw = 8;
@@ -65,6 +66,8 @@ static int stream_shape(int64_t rx, int64_t ry, size_t elem, uint32_t* stage_byt
       cw = c;
       break;
     }
+  cw = std::min(cw, cw_cap);
+  while (32 * cw < txv) cw *= 2;
   int64_t ch = (32 * cw / txv) * 4;
   if (ch <= 0) return 0;
   ch = std::min(ch, ry);
@@ -150,6 +153,82 @@ static int64_t face_points_host(const BlockHost& b, int f) {
   return b.extent[0] * b.extent[1];
 }
 
+// Work items of a plan's blocks for one shape.  Blocks that fit the
+// plane-streaming path get one item per row window and z-chunk; the others
+// one item per TX x TY tile and z-chunk.  The chunk is a power-of-two fraction
+// of the tallest block: zc_req (> 0, clamped to the tallest block), else the
+// cost model's choice (choose_chunk) for a handle, or the longest that still
+// gives at least `target_items` items (down to min_chunk planes, at least 2).
+int plan_items(Plan* P, int64_t zc_req, int cw_cap, int64_t target_items, int64_t min_chunk) {
+  std::vector<int> warps(P->blocks.size());
+  std::vector<int64_t> chunks(P->blocks.size());
+  int64_t units = 0, maxz = 0;
+  P->max_stage = 0;
+  for (size_t b = 0; b < P->blocks.size(); ++b) {
+    BlockHost& B = P->blocks[b];
+    uint32_t sb = 0;
+    int64_t ch = 0;
+    const int cw = stream_shape(B.rx, B.ry, P->elem, cw_cap, &sb, &ch);
+    warps[b] = cw;
+    chunks[b] = ch;
+    if (cw) P->max_stage = std::max(P->max_stage, sb);
+    units += cw ? (B.ry + ch - 1) / ch : ((B.extent[0] + TX - 1) / TX) * ((B.extent[1] + TY - 1) / TY);
+    maxz = std::max(maxz, B.extent[2]);
+  }
+  // the cost model may go down to single planes (a small problem that fits
+  // one wave); the item-target rule stops at 2
+  const int64_t zmin = std::max<int64_t>(min_chunk, target_items > 0 ? 2 : 1);
+  int64_t zc = maxz;
+  if (zc_req > 0) {
+    zc = std::min(zc_req, maxz);
+  } else if (target_items > 0) {
+    while (zc > zmin && (zc + 1) / 2 >= zmin && units * ((maxz + zc - 1) / zc) < target_items) zc = (zc + 1) / 2;
+  } else {
+    zc = choose_chunk(*P, warps, chunks, maxz, zmin);
+  }
+  P->zchunk = zc;
+  P->cw_cap = cw_cap;
+  P->n_units = 0;
+  for (const BlockHost& B : P->blocks) P->n_units += (B.extent[2] + zc - 1) / zc;
+  P->items.clear();
+  for (GridHost& G : P->grids) {
+    G.item_begin = (int64_t)P->items.size();
+    for (int64_t b = G.block_begin; b < G.block_end; ++b) {
+      BlockHost& B = P->blocks[b];
+      const int cw = warps[b];
+      B.item_begin = (int64_t)P->items.size();
+      for (int64_t z0 = 0; z0 < B.extent[2]; z0 += zc) {
+        WorkItem w;
+        w.block = (int32_t)b;
+        w.z0 = (int16_t)z0;
+        w.z1 = (int16_t)std::min(B.extent[2], z0 + zc);
+        w.ya = w.yb = 0;
+        if (cw) {
+          for (int64_t ya = 0; ya < B.ry; ya += chunks[b]) {
+            w.slot = (int32_t)P->items.size();
+            w.x0 = -1;
+            w.y0 = (int16_t)(cw | (B.rx != B.extent[0] || B.ry != B.extent[1] ? kItemRagged : 0));
+            w.ya = (int16_t)ya;
+            w.yb = (int16_t)std::min(B.ry, ya + chunks[b]);
+            P->items.push_back(w);
+          }
+          continue;
+        }
+        for (int64_t y0 = 0; y0 < B.extent[1]; y0 += TY)
+          for (int64_t x0 = 0; x0 < B.extent[0]; x0 += TX) {
+            w.slot = (int32_t)P->items.size();
+            w.x0 = (int16_t)x0;
+            w.y0 = (int16_t)y0;
+            P->items.push_back(w);
+          }
+      }
+      B.item_end = (int64_t)P->items.size();
+    }
+    G.item_end = (int64_t)P->items.size();
+  }
+  return JACOBI_OK;
+}
+
 int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* splits, jacobi_dtype dtype,
                const jacobi_init* inits, Plan* P, int64_t target_items, int64_t min_chunk) {
   if (n_grids < 1 || !grids || !splits) return set_error(JACOBI_EINVAL, "need at least one grid");
@@ -215,77 +294,29 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
     P->n_points += d.nx * d.ny * d.nz;
     P->grids.push_back(G);
   }
-  // Work items.  Blocks that fit the plane-streaming path get one item per
-  // row window and z-chunk; the others one item per TX x TY tile and z-chunk.
-  // The chunk is a power-of-two fraction of the tallest block: chosen by the
-  // cost model (choose_chunk) for a handle, or the longest that still gives
-  // at least `target_items` items (down to min_chunk planes, at least 2).
-  std::vector<int> warps(P->blocks.size());
-  std::vector<int64_t> chunks(P->blocks.size());
-  int64_t units = 0, maxz = 0;
+  // padded rows (a whole number of 16-byte vectors) and planes (of 4-row groups)
   const int64_t vec = 16 / (int64_t)P->elem;
-  for (size_t b = 0; b < P->blocks.size(); ++b) {
-    BlockHost& B = P->blocks[b];
+  for (BlockHost& B : P->blocks) {
     B.rx = (B.extent[0] + vec - 1) / vec * vec;
     B.ry = (B.extent[1] + 3) / 4 * 4;
-    uint32_t sb = 0;
-    int64_t ch = 0;
-    const int cw = stream_shape(B.rx, B.ry, P->elem, &sb, &ch);
-    warps[b] = cw;
-    chunks[b] = ch;
-    if (cw) P->max_stage = std::max(P->max_stage, sb);
-    units += cw ? (B.ry + ch - 1) / ch : ((B.extent[0] + TX - 1) / TX) * ((B.extent[1] + TY - 1) / TY);
-    maxz = std::max(maxz, B.extent[2]);
   }
-  // the cost model may go down to single planes (a small problem that fits
-  // one wave); the item-target rule stops at 2
-  const int64_t zmin = std::max<int64_t>(min_chunk, target_items > 0 ? 2 : 1);
-  int64_t zc = maxz;
-  if (target_items > 0) {
-    while (zc > zmin && (zc + 1) / 2 >= zmin && units * ((maxz + zc - 1) / zc) < target_items) zc = (zc + 1) / 2;
-  } else {
-    zc = choose_chunk(*P, warps, chunks, maxz, zmin);
+  int rc = plan_items(P, 0, 8, target_items, min_chunk);
+  if (rc) return rc;
+  // Table capacity: the item and unit tables are sized for the finest shape
+  // jacobi_set_shape accepts and the autotuner tries (z-chunks down to a
+  // quarter of the planned one, CTAs down to 2 consumer warps), so a handle
+  // can be re-planned in place; states and slots never move.
+  P->cap_items = (int64_t)P->items.size();
+  P->cap_units = P->n_units;
+  if (target_items <= 0) {
+    Plan probe = *P;
+    rc = plan_items(&probe, std::max<int64_t>(1, P->zchunk / 4), 2, 0, 1);
+    if (rc) return rc;
+    P->cap_items = std::max(P->cap_items, (int64_t)probe.items.size());
+    P->cap_units = std::max(P->cap_units, probe.n_units);
   }
-  P->zchunk = zc;
-  P->n_units = 0;
-  for (const BlockHost& B : P->blocks) P->n_units += (B.extent[2] + zc - 1) / zc;
-  for (GridHost& G : P->grids) {
-    G.item_begin = (int64_t)P->items.size();
-    for (int64_t b = G.block_begin; b < G.block_end; ++b) {
-      BlockHost& B = P->blocks[b];
-      const int cw = warps[b];
-      B.item_begin = (int64_t)P->items.size();
-      for (int64_t z0 = 0; z0 < B.extent[2]; z0 += zc) {
-        WorkItem w;
-        w.block = (int32_t)b;
-        w.z0 = (int16_t)z0;
-        w.z1 = (int16_t)std::min(B.extent[2], z0 + zc);
-        w.ya = w.yb = 0;
-        if (cw) {
-          for (int64_t ya = 0; ya < B.ry; ya += chunks[b]) {
-            w.slot = (int32_t)P->items.size();
-            w.x0 = -1;
-            w.y0 = (int16_t)(cw | (B.rx != B.extent[0] || B.ry != B.extent[1] ? kItemRagged : 0));
-            w.ya = (int16_t)ya;
-            w.yb = (int16_t)std::min(B.ry, ya + chunks[b]);
-            P->items.push_back(w);
-          }
-          continue;
-        }
-        for (int64_t y0 = 0; y0 < B.extent[1]; y0 += TY)
-          for (int64_t x0 = 0; x0 < B.extent[0]; x0 += TX) {
-            w.slot = (int32_t)P->items.size();
-            w.x0 = (int16_t)x0;
-            w.y0 = (int16_t)y0;
-            P->items.push_back(w);
-          }
-      }
-      B.item_end = (int64_t)P->items.size();
-    }
-    G.item_end = (int64_t)P->items.size();
-  }
-  if ((int64_t)P->items.size() > (1ll << 30)) return set_error(JACOBI_EINVAL, "too many work items");
-  const int64_t nb = (int64_t)P->blocks.size(), ni = (int64_t)P->items.size(), ng = n_grids;
+  if (P->cap_items > (1ll << 30)) return set_error(JACOBI_EINVAL, "too many work items");
+  const int64_t nb = (int64_t)P->blocks.size(), ni = P->cap_items, ng = n_grids;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, A); return o; };
   P->off_blocks = take(nb * sizeof(BlockDev));
@@ -298,7 +329,7 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
   P->off_inits = take(ng * sizeof(InitDev));
   P->off_gids = take(ng * sizeof(int32_t));
   P->off_partials = take(ni * sizeof(double));
-  const int64_t nu = P->n_units;
+  const int64_t nu = P->cap_units;
   P->off_progress = take(nu * sizeof(int64_t));
   P->off_err = take(64);
   P->off_stage_tab = take(nb * 6 * sizeof(void*));
@@ -307,6 +338,7 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
   P->off_pdep_off = take((nu + 1) * sizeof(int32_t));
   P->off_pdep_ids = take(8 * nu * sizeof(int32_t));
   P->off_active_blocks = take(nb * sizeof(int32_t));
+  P->off_it0 = take(sizeof(int64_t));
   const size_t per16 = 32;  // plane pitch rounded to 32 elements
   for (auto& B : P->blocks) {
     B.pitch = (int64_t)align_up((size_t)(B.rx * B.ry), per16);
@@ -602,6 +634,7 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
   a.n_units = (int32_t)h->active_units.size();
   a.grids = h->d_grids;
   a.it0 = it0;
+  a.it0_dev = nullptr;
   a.n_iters = n;
   a.progress = h->d_progress;
   a.err = h->d_err;
@@ -615,6 +648,61 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
   a.emu = h->fp64_emu;
   a.pad_ = 0;
   const int ctas = std::min(maxc, a.n_units);
+  // Replay a captured graph of the same launch shape; the start iteration
+  // goes to device memory first (a pageable source is staged before the call
+  // returns, so the stack variable may go).
+  jacobi_s::PersistGraph& pg = h->pgraph[resid_first ? 1 : 0];
+  if (!h->pgraph_off && (!pg.exec || pg.n_iters != n || pg.n_units != a.n_units || pg.stages != a.stages ||
+                         pg.ctas != ctas)) {
+    if (pg.exec) cudaGraphExecDestroy(pg.exec);
+    pg.exec = nullptr;
+    PersistLaunch c = a;
+    c.it0_dev = h->d_it0;
+    cudaStream_t cs = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = launch_persistent(c, ctas, cs);
+      cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+      e = e1 != cudaSuccess ? e1 : e2;
+    }
+    if (e == cudaSuccess) {
+      // the graph must hold exactly the one kernel node, launched
+      // cooperatively (its CTAs wait on each other's flags)
+      cudaGraphNode_t node = nullptr;
+      size_t nn = 1;
+      cudaGraphNodeType ty;
+      e = cudaGraphGetNodes(g, &node, &nn);
+      if (e == cudaSuccess && (nn != 1 || cudaGraphNodeGetType(node, &ty) != cudaSuccess ||
+                               ty != cudaGraphNodeTypeKernel))
+        e = cudaErrorNotSupported;
+      if (e == cudaSuccess) {
+        cudaLaunchAttributeValue v{};
+        v.cooperative = 1;
+        e = cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributeCooperative, &v);
+      }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&pg.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // a refused capture leaves no sticky error; launch directly from now on
+      pg.exec = nullptr;
+      h->pgraph_off = true;
+    } else {
+      pg.n_iters = n;
+      pg.n_units = a.n_units;
+      pg.stages = a.stages;
+      pg.ctas = ctas;
+    }
+  }
+  if (!h->pgraph_off && pg.exec) {
+    const int64_t v = it0;
+    JGB_CUDA(cudaMemcpyAsync(h->d_it0, &v, sizeof v, cudaMemcpyHostToDevice, s));
+    JGB_CUDA(cudaGraphLaunch(pg.exec, s));
+    return JACOBI_OK;
+  }
   JGB_CUDA(launch_persistent(a, ctas, s));
   return JACOBI_OK;
 }
@@ -831,6 +919,43 @@ void activate_grid(jacobi_t* h, int64_t g) {
   h->tables_dirty = true;
 }
 
+// Re-plan the work items of a live handle for another shape (the states,
+// slots and every table offset stay where they are; the item and unit tables
+// were sized for the finest accepted shape).  Recomputes |b| (its summation
+// order follows the items) and drops captured graphs.
+int apply_shape(jacobi_t* h, int64_t zchunk, int32_t cw_cap, cudaStream_t s) {
+  if (zchunk < 0 || (cw_cap != 2 && cw_cap != 4 && cw_cap != 8))
+    return set_error(JACOBI_EINVAL, "bad shape: zchunk %lld, cw_cap %d", (long long)zchunk, cw_cap);
+  Plan Q = h->plan;
+  int rc = plan_items(&Q, zchunk, cw_cap, 0, 1);
+  if (rc) return rc;
+  if ((int64_t)Q.items.size() > Q.cap_items || Q.n_units > Q.cap_units)
+    return set_error(JACOBI_EINVAL, "shape (zchunk %lld, cw_cap %d) needs %lld items / %lld units; the tables hold "
+                     "%lld / %lld", (long long)zchunk, cw_cap, (long long)Q.items.size(), (long long)Q.n_units,
+                     (long long)Q.cap_items, (long long)Q.cap_units);
+  JGB_CUDA(cudaStreamSynchronize(s));  // no launch may still read the old items
+  h->plan = std::move(Q);
+  const Plan& P = h->plan;
+  for (size_t g = 0; g < P.grids.size(); ++g) {
+    h->h_grids[g].item_begin = (int32_t)P.grids[g].item_begin;
+    h->h_grids[g].item_end = (int32_t)P.grids[g].item_end;
+  }
+  JGB_CUDA(cudaMemcpyAsync(h->d_items, P.items.data(), P.items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
+  JGB_CUDA(cudaMemcpyAsync(h->d_grids, h->h_grids, P.grids.size() * sizeof(GridDev), cudaMemcpyHostToDevice, s));
+  JGB_CUDA(cudaMemsetAsync(h->d_progress, 0, P.cap_units * sizeof(int64_t), s));
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+  for (auto& pg : h->pgraph) {
+    if (pg.exec) cudaGraphExecDestroy(pg.exec);
+    pg = jacobi_s::PersistGraph();
+  }
+  if (128 + h->stages * (int64_t)P.max_stage > kMaxStepSmem) h->stages = 3;
+  h->tables_dirty = true;
+  rc = compute_bnorm(h, s, -1);
+  if (rc) return rc;
+  return refresh_active(h, s);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -970,6 +1095,7 @@ int jacobi_create_batch(int64_t n_grids, const jacobi_dim3* grids, const jacobi_
   h->d_pdep_off = (int32_t*)(h->ws + P.off_pdep_off);
   h->d_pdep_ids = (int32_t*)(h->ws + P.off_pdep_ids);
   h->d_active_blocks = (int32_t*)(h->ws + P.off_active_blocks);
+  h->d_it0 = (int64_t*)(h->ws + P.off_it0);
   if (const char* w = getenv("JACOBI_WAIT_MS")) {
     const double ms = atof(w);
     if (ms > 0) h->wait_ns = (uint64_t)(ms * 1e6);
@@ -1010,6 +1136,8 @@ int jacobi_destroy(jacobi_t* h) {
   cudaDeviceSynchronize();
   for (channel_s* c : std::vector<channel_s*>(h->channels)) channel_close(c);
   if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (auto& pg : h->pgraph)
+    if (pg.exec) cudaGraphExecDestroy(pg.exec);
   kind_fork_destroy(&h->fork);
   if (h->stage) cudaFree(h->stage);
   if (h->d_desc) cudaFree(h->d_desc);
@@ -1039,6 +1167,9 @@ int jacobi_info(const jacobi_t* h, jacobi_info_t* out) {
   for (int k = 0; k < kItemKinds; ++k) kinds += h->kind_off[k + 1] > h->kind_off[k] ? 1 : 0;
   out->item_kinds = kinds;
   for (int k = 0; k < 8; ++k) out->kind_items[k] = k < kItemKinds ? h->kind_off[k + 1] - h->kind_off[k] : 0;
+  out->zchunk = h->plan.zchunk;
+  out->cw_cap = h->plan.cw_cap;
+  out->pad2_ = 0;
   return JACOBI_OK;
 }
 
@@ -1062,34 +1193,44 @@ uint64_t geometry_signature(const Plan& P) {
   return x;
 }
 
-bool cache_lookup(uint64_t key, int32_t* path, int32_t* stages, double* ms) {
+// Cache lines: "v2 <signature> <path> <stages> <zchunk> <cw_cap> <ms per iteration>".
+bool cache_lookup(uint64_t key, jacobi_tune_result* r) {
   const char* f = getenv("JACOBI_TUNE_CACHE");
   if (!f || !*f) return false;
   FILE* fp = fopen(f, "r");
   if (!fp) return false;
-  unsigned long long k;
-  int p, st;
-  double t;
+  char line[256];
   bool found = false;
-  while (fscanf(fp, "%llx %d %d %lf", &k, &p, &st, &t) == 4)
-    if (k == key) {
-      *path = p; *stages = st; *ms = t;
+  while (fgets(line, sizeof line, fp)) {
+    unsigned long long k;
+    int p, st, cw;
+    long long zc;
+    double t;
+    if (sscanf(line, "v2 %llx %d %d %lld %d %lf", &k, &p, &st, &zc, &cw, &t) == 6 && k == key) {
+      r->path = p; r->stages = st; r->zchunk = zc; r->cw_cap = cw; r->ms_per_iter = t;
       found = true;  // the last entry wins
     }
+  }
   fclose(fp);
   return found;
 }
 
-void cache_store(uint64_t key, int32_t path, int32_t stages, double ms) {
+void cache_store(uint64_t key, const jacobi_tune_result& r) {
   const char* f = getenv("JACOBI_TUNE_CACHE");
   if (!f || !*f) return;
   FILE* fp = fopen(f, "a");
   if (!fp) return;
-  fprintf(fp, "%016llx %d %d %.6f\n", (unsigned long long)key, path, stages, ms);
+  fprintf(fp, "v2 %016llx %d %d %lld %d %.6f\n", (unsigned long long)key, r.path, r.stages, (long long)r.zchunk,
+          r.cw_cap, r.ms_per_iter);
   fclose(fp);
 }
 
 }  // namespace
+
+extern "C" int jacobi_set_shape(jacobi_t* h, int64_t zchunk, int32_t cw_cap, void* stream) {
+  if (!h) return set_error(JACOBI_EINVAL, "null handle");
+  return apply_shape(h, zchunk, cw_cap, S(stream));
+}
 
 extern "C" int jacobi_autotune(jacobi_t* h, int64_t iters_per_trial, void* stream, jacobi_tune_result* out) {
   if (!h || iters_per_trial < 1) return set_error(JACOBI_EINVAL, "bad arguments to jacobi_autotune");
@@ -1097,7 +1238,7 @@ extern "C" int jacobi_autotune(jacobi_t* h, int64_t iters_per_trial, void* strea
   const Plan& P = h->plan;
   const uint64_t key = geometry_signature(P);
   jacobi_tune_result r{};
-  if (cache_lookup(key, &r.path, &r.stages, &r.ms_per_iter)) {
+  if (cache_lookup(key, &r)) {
     r.from_cache = 1;
   } else {
     std::vector<jacobi_dim3> grids;
@@ -1116,56 +1257,80 @@ extern "C" int jacobi_autotune(jacobi_t* h, int64_t iters_per_trial, void* strea
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     double best = INFINITY;
-    const int32_t paths[3] = {JACOBI_PATH_GRAPH, JACOBI_PATH_PERSISTENT, JACOBI_PATH_FUSED};
-    for (int32_t path : paths) {
-      for (int32_t st = 3; st <= 6; ++st) {
-        // the ring depth is a choice of the persistent kernel only
-        if (path != JACOBI_PATH_PERSISTENT && st != kStreamStages) continue;
-        if (128 + st * (int64_t)P.max_stage > kMaxStepSmem) continue;
-        if (P.max_stage == 0 && st != 3) continue;  // no plane-streamed blocks: the depth is irrelevant
-        t->stages = st;
-        t->path = path;
-        t->tables_dirty = true;
-        rc = do_step(t, std::max<int64_t>(iters_per_trial / 4, 2), s);  // warm-up (graph capture etc.)
-        if (!rc && cudaEventRecord(e0, s) != cudaSuccess) rc = JACOBI_ECUDA;
-        if (!rc) rc = do_step(t, iters_per_trial, s);
-        if (!rc && cudaEventRecord(e1, s) != cudaSuccess) rc = JACOBI_ECUDA;
-        if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = JACOBI_ECUDA;
-        if (!rc) rc = check_err_word(t, s);
-        if (rc) {
-          cudaEventDestroy(e0);
-          cudaEventDestroy(e1);
-          jacobi_destroy(t);
-          return rc;
-        }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        const double per = ms / (double)iters_per_trial;
-        r.n_tried += 1;
-        if (per < best) {
-          best = per;
-          r.path = path;
-          r.stages = st;
-          r.ms_per_iter = per;
-        }
-        if (t->graph) {
-          cudaGraphExecDestroy(t->graph);
-          t->graph = nullptr;
-        }
+    // Candidate shapes: the cost model's z-chunk, twice, half and a quarter of
+    // it; CTAs of up to 8, 4 or 2 consumer warps (row windows of the
+    // corresponding height).  Shapes that plan the same items are tried once.
+    const int64_t zc0 = t->plan.zchunk;
+    std::vector<std::pair<int64_t, int32_t>> shapes;
+    std::vector<std::vector<WorkItem>> seen;
+    for (int64_t zc : {zc0, 2 * zc0, std::max<int64_t>(1, zc0 / 2), std::max<int64_t>(1, zc0 / 4)})
+      for (int32_t cw : {8, 4, 2}) {
+        Plan q = t->plan;
+        if (plan_items(&q, zc, cw, 0, 1) || (int64_t)q.items.size() > q.cap_items || q.n_units > q.cap_units) continue;
+        bool dup = false;
+        for (const auto& v : seen)
+          dup = dup || (v.size() == q.items.size() &&
+                        std::equal(v.begin(), v.end(), q.items.begin(), [](const WorkItem& a, const WorkItem& b) {
+                          return a.block == b.block && a.x0 == b.x0 && a.y0 == b.y0 && a.z0 == b.z0 && a.z1 == b.z1 &&
+                                 a.ya == b.ya && a.yb == b.yb;
+                        }));
+        if (dup) continue;
+        seen.push_back(q.items);
+        shapes.push_back({zc, cw});
       }
+    auto trial = [&](int32_t path, int32_t st, int64_t zc, int32_t cw) -> int {
+      int rc2 = apply_shape(t, zc, cw, s);
+      if (rc2) return rc2;
+      t->stages = st;
+      t->path = path;
+      t->tables_dirty = true;
+      rc2 = do_step(t, std::max<int64_t>(iters_per_trial / 4, 2), s);  // warm-up (graph capture etc.)
+      if (!rc2 && cudaEventRecord(e0, s) != cudaSuccess) rc2 = JACOBI_ECUDA;
+      if (!rc2) rc2 = do_step(t, iters_per_trial, s);
+      if (!rc2 && cudaEventRecord(e1, s) != cudaSuccess) rc2 = JACOBI_ECUDA;
+      if (!rc2 && cudaEventSynchronize(e1) != cudaSuccess) rc2 = JACOBI_ECUDA;
+      if (!rc2) rc2 = check_err_word(t, s);
+      if (rc2) return rc2;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double per = ms / (double)iters_per_trial;
+      r.n_tried += 1;
+      if (per < best) {
+        best = per;
+        r.path = path;
+        r.stages = st;
+        r.zchunk = zc;
+        r.cw_cap = cw;
+        r.ms_per_iter = per;
+      }
+      return JACOBI_OK;
+    };
+    // every shape on the graph path and on the persistent kernel (4 stages),
+    // then the fused path and the other ring depths at the best shape
+    for (const auto& sh : shapes)
+      for (int32_t path : {(int32_t)JACOBI_PATH_GRAPH, (int32_t)JACOBI_PATH_PERSISTENT})
+        if (!rc) rc = trial(path, kStreamStages, sh.first, sh.second);
+    const int64_t bz = r.zchunk;
+    const int32_t bc = r.cw_cap;
+    if (!rc) rc = trial(JACOBI_PATH_FUSED, kStreamStages, bz, bc);
+    for (int32_t st = 3; st <= 6 && !rc; ++st) {
+      if (st == kStreamStages || t->plan.max_stage == 0) continue;  // no plane-streamed blocks: depth irrelevant
+      Plan q = t->plan;
+      plan_items(&q, bz, bc, 0, 1);
+      if (128 + st * (int64_t)q.max_stage > kMaxStepSmem) continue;
+      rc = trial(JACOBI_PATH_PERSISTENT, st, bz, bc);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     jacobi_destroy(t);
-    cache_store(key, r.path, r.stages, r.ms_per_iter);
+    if (rc) return rc;
+    cache_store(key, r);
   }
+  int rc = apply_shape(h, r.zchunk, r.cw_cap, s);
+  if (rc) return rc;
   h->path = r.path;
   h->stages = r.stages;
   h->tables_dirty = true;
-  if (h->graph) {
-    cudaGraphExecDestroy(h->graph);
-    h->graph = nullptr;
-  }
   if (out) *out = r;
   return JACOBI_OK;
 }

@@ -126,12 +126,18 @@ __global__ void k_chan_send_direct(ChanCtr* c, int to, uint32_t n, const void* s
   copy16(dst, src, bytes, (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    const uint32_t prev = atomicAdd(&c->done[to], 1u);
-    if (prev == gridDim.x - 1) {
-      c->done[to] = 0;
-      c->size[to][n & 1] = bytes;
+    // one CTA: its barrier already orders every copy before the release
+    // store; several: the last CTA to finish publishes
+    bool last = gridDim.x == 1;
+    if (!last) {
       __threadfence();
+      last = atomicAdd(&c->done[to], 1u) == gridDim.x - 1;
+      if (last) {
+        c->done[to] = 0;
+        __threadfence();
+      }
+    }
+    if (last) {
       st_release_u32(&c->delivered[to], n + 1);
       st_release_u32(&c->consumed[to], n + 1);
     }

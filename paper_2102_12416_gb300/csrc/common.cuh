@@ -269,6 +269,8 @@ __device__ __forceinline__ double widen_f32(float f) {
 // with acquire semantics.  Returns true on success.  On expiry it records
 // DEV_TIMEOUT in *err (first failure wins); it also gives up early when another
 // waiter has already recorded an error, so one failure stops every waiter.
+// The first polls spin without sleeping (a neighbour's flag usually arrives
+// within a few L2 round trips); after that the poll backs off to 256 ns.
 __device__ inline bool wait_ge(const int64_t* flag, int64_t target, uint32_t* err,
                                uint64_t limit_ns) {
   if (ld_acquire(flag) >= target) return true;
@@ -276,10 +278,13 @@ __device__ inline bool wait_ge(const int64_t* flag, int64_t target, uint32_t* er
   unsigned sleep = 32;
   for (uint32_t n = 0; n < (1u << 26); ++n) {
     if (ld_acquire(flag) >= target) return true;
+    if ((n & 7u) != 7u && n < 64u) continue;
     if (ld_volatile_u32(err) != DEV_OK) return false;
     if (globaltimer_ns() - t0 > limit_ns) break;
-    __nanosleep(sleep);
-    if (sleep < 512) sleep <<= 1;
+    if (n >= 64u) {
+      __nanosleep(sleep);
+      if (sleep < 256) sleep <<= 1;
+    }
   }
   atomicCAS(err, (uint32_t)DEV_OK, (uint32_t)DEV_TIMEOUT);
   return false;

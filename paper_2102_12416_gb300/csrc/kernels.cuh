@@ -23,8 +23,9 @@ struct BlockGeom {
 };
 
 // Largest dynamic shared memory a step kernel may use (sm_103a opt-in limit of
-// 227 KB per CTA, minus room for the kernels' static shared memory).
-constexpr int kMaxStepSmem = 227 * 1024 - 1024;  // 1 KB left for static shared memory
+// 227 KB per CTA, minus room for the kernels' static shared memory: the
+// persistent kernel keeps its units' tables there, about 3.5 KB).
+constexpr int kMaxStepSmem = 227 * 1024 - 4096;
 
 // A plane-streaming item encodes its consumer warps (2, 4 or 8) in the low
 // bits of y0 and, in bit 4, whether its block has padding (ragged rows or
@@ -142,6 +143,7 @@ struct PersistLaunch {
   int32_t n_units;             // active units
   const GridDev* grids;
   int64_t it0;
+  const int64_t* it0_dev;      // when set, the start iteration is read here (graph replays)
   int64_t n_iters;
   int64_t* progress;           // per unit: iterations completed (absolute)
   uint32_t* err;

@@ -62,11 +62,14 @@ struct Plan {
   int64_t halo_elems = 0;  // face elements moved per iteration (internal faces)
   uint32_t max_stage = 0;  // largest ring stage (bytes) of a plane-streamed block
   int64_t zchunk = 1;      // planes per z-chunk (the last chunk of a block may be shorter)
+  int32_t cw_cap = 8;      // most consumer warps per streaming CTA (sets the row windows)
   int64_t n_units = 0;     // persistent-kernel units: (block, z-chunk) pairs
+  int64_t cap_items = 0;   // item / unit table capacity in the workspace (the finest shape)
+  int64_t cap_units = 0;
   // byte offsets into the workspace
   size_t off_blocks, off_geom, off_items, off_active, off_kind, off_grids, off_norms, off_inits, off_gids, off_partials,
       off_progress, off_err, off_stage_tab, off_punit_items, off_punit_ids, off_pdep_off, off_pdep_ids,
-      off_active_blocks;
+      off_active_blocks, off_it0;
   size_t off_stage_begin = 0, off_stage_end = 0;  // the explicit-path staging buffers, contiguous
   int64_t halo_faces = 0;                         // internal faces (one message each per iteration)
   size_t bytes = 0;
@@ -84,6 +87,9 @@ constexpr int kMaxBlockExtent = JACOBI_MAX_BLOCK_EXTENT;
 constexpr int64_t kServeMinChunk = 16;
 int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* splits, jacobi_dtype dtype,
                const jacobi_init* inits, Plan* out, int64_t target_items = 0, int64_t min_chunk = 1);
+// Rebuild the work items of a built plan for another shape (z-chunk zc_req,
+// 0 = the cost model's; at most cw_cap consumer warps per streaming CTA).
+int plan_items(Plan* P, int64_t zc_req, int cw_cap, int64_t target_items, int64_t min_chunk);
 
 // Device block table entries of a plan whose workspace starts at `ws`; block
 // and neighbour ids are offset by `base`; grid_override >= 0 replaces every
@@ -124,6 +130,7 @@ struct jacobi_s {
   int32_t* d_pdep_off = nullptr;
   int32_t* d_pdep_ids = nullptr;
   int32_t* d_active_blocks = nullptr;  // blocks of the active grids (exchange kernels)
+  int64_t* d_it0 = nullptr;            // start iteration of a replayed persistent graph
 
   // host mirrors
   std::vector<jgb::WorkItem> active_items;
@@ -147,6 +154,15 @@ struct jacobi_s {
   cudaGraphExec_t graph = nullptr;
   int64_t graph_iters = 0;
   int32_t graph_items = -1;
+  // PERSISTENT path: the cooperative launch captured once per shape (without /
+  // with the fused residual of the first iteration) and replayed; the start
+  // iteration comes from d_it0
+  struct PersistGraph {
+    cudaGraphExec_t exec = nullptr;
+    int64_t n_iters = 0;
+    int32_t n_units = -1, stages = 0, ctas = 0;
+  } pgraph[2];
+  bool pgraph_off = false;        // capture of the cooperative launch failed: launch directly
 
   uint64_t wait_ns = 1000000000ull;
   int32_t stages = 4;             // ring stages of the plane-streaming path

@@ -452,7 +452,7 @@ __device__ __forceinline__ double stream_plane(const PlaneView<T>& O, int k, int
 // expired (the error word is set and issued copies drained).
 template <typename T, int RY, int MODE>
 __device__ double stream_item(const BlockDev& B, int p, const WorkItem& w, Ring& ring, uint32_t* err,
-                              uint64_t wait_ns, bool emu, bool& ok) {
+                              uint64_t wait_ns, bool emu, bool& ok, void* const* tab) {
   constexpr int VEC = V16<T>::N;
   const int tid = threadIdx.x;
   const int txv = B.rx / VEC;
@@ -461,7 +461,8 @@ __device__ double stream_item(const BlockDev& B, int p, const WorkItem& w, Ring&
   const bool rag = item_ragged(w);
   const int S = ring.S;
   const StageLayout L = stage_layout<T>(B, w.ya, w.yb);
-  const PlaneView<T> O = plane_view<T>(B, p);
+  PlaneView<T> O = plane_view<T>(B, p);
+  O.ss = tab;
   const int nplanes = w.z1 - w.z0 + 2;
   auto issue = [&](int q) {
     const int st = q % S;
@@ -499,11 +500,11 @@ __device__ double stream_item(const BlockDev& B, int p, const WorkItem& w, Ring&
       const unsigned char* sp = ring.stages + (size_t)((q + 1) % S) * L.bytes;
       const int kq = w.z0 - 1 + q;
       if (rag) {
-        if (sizeof(T) == 8 && emu) acc += stream_plane<T, RY, MODE, true, true, false>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
-        else acc += stream_plane<T, RY, MODE, false, true, false>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+        if (sizeof(T) == 8 && emu) acc += stream_plane<T, RY, MODE, true, true, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+        else acc += stream_plane<T, RY, MODE, false, true, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
       } else {
-        if (sizeof(T) == 8 && emu) acc += stream_plane<T, RY, MODE, true, false, false>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
-        else acc += stream_plane<T, RY, MODE, false, false, false>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+        if (sizeof(T) == 8 && emu) acc += stream_plane<T, RY, MODE, true, false, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+        else acc += stream_plane<T, RY, MODE, false, false, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
       }
     }
   }
@@ -524,12 +525,13 @@ __device__ double stream_item(const BlockDev& B, int p, const WorkItem& w, Ring&
   return acc;
 }
 
+// `tab` holds the block's six send slots for the new iterate (shared memory).
 template <typename T, int MODE>
 __device__ double run_item(const BlockDev& B, int p, const WorkItem& w, Ring& ring, uint32_t* err,
-                           uint64_t wait_ns, bool emu, bool& ok) {
+                           uint64_t wait_ns, bool emu, bool& ok, void* const* tab) {
   ok = true;
   if (w.x0 >= 0) return tile_sweep<T, MODE>(B, p, w.x0, w.y0, w.z0, w.z1, threadIdx.x % TX, threadIdx.x / TX);
-  return stream_item<T, 4, MODE>(B, p, w, ring, err, wait_ns, emu, ok);
+  return stream_item<T, 4, MODE>(B, p, w, ring, err, wait_ns, emu, ok, tab);
 }
 
 __device__ __forceinline__ Ring ring_setup(unsigned char* smem, int S) {
@@ -695,62 +697,128 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, StreamShape<CW>::min
 // adjacent chunks, the same chunk of the x and y neighbours, the facing chunk
 // of the z neighbours).  Waits are bounded: on expiry the error word is set and
 // every CTA leaves at its next wait.
+// A CTA that owns at most kPersistCache units copies their tables (block
+// entry, send slots by parity, item range, partners, grid start, FP64 adder
+// flag) into shared memory once, so an iteration starts with its flag polls
+// instead of a chain of dependent table loads from L2 (same-box A/B in the
+// notes of the library's design).
 // Proxy fences order the generic stores of neighbours (and of this CTA's
-// previous iteration) before the bulk copies that read them.
+// previous iteration) before the bulk copies that read them; the release
+// store after the CTA barrier is cumulative, so it publishes every thread's
+// stores without a separate fence.
 // ---------------------------------------------------------------------------
+constexpr int kPersistCache = 8;
+constexpr int kPersistDeps = 8;  // a unit has at most 6 partners
+
+struct UnitCache {
+  BlockDev B;
+  void* send[2][6];      // send slots for a new iterate of parity 0 / 1
+  int64_t start_iter;    // the block's grid start
+  int32_t unit, q0, q1, ndep;
+  int32_t dep[kPersistDeps];
+  int32_t emu;
+  int32_t pad_;
+};
+static_assert(kPersistCache * sizeof(UnitCache) + 512 <= 227 * 1024 - kMaxStepSmem,
+              "the persistent kernel's static shared memory must fit beside the largest ring");
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_persist(PersistLaunch a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double red[kThreads / 32];
   __shared__ int s_ok;
-  const int tid = threadIdx.x;
-  Ring ring = ring_setup(smem, a.stages);
+  __shared__ UnitCache s_u[kPersistCache];
+  __shared__ void* s_tab[6];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int G = (int)gridDim.x;
+  const int mine = a.n_units > (int)blockIdx.x ? (a.n_units - (int)blockIdx.x + G - 1) / G : 0;
+  const bool cached = mine <= kPersistCache;
+  if (cached) {
+    for (int k = tid >> 5; k < mine; k += kThreads / 32) {  // one warp per unit
+      const int ui = (int)blockIdx.x + k * G;
+      UnitCache& U = s_u[k];
+      const int q0 = a.unit_items[ui];
+      const BlockDev* Bg = a.blocks + a.items[q0].block;
+      const uint32_t* src = (const uint32_t*)Bg;
+      uint32_t* dst = (uint32_t*)&U.B;
+      for (int i = lane; i < (int)(sizeof(BlockDev) / 4); i += 32) dst[i] = src[i];
+      if (lane < 12) U.send[lane / 6][lane % 6] = Bg->send[lane % 6][lane / 6];
+      const int d0 = a.dep_off[ui], d1 = a.dep_off[ui + 1];
+      if (lane < kPersistDeps) U.dep[lane] = d0 + lane < d1 ? a.dep_ids[d0 + lane] : 0;
+      if (lane == 0) {
+        U.unit = a.unit_ids[ui];
+        U.q0 = q0;
+        U.q1 = a.unit_items[ui + 1];
+        U.ndep = d1 - d0;
+        U.start_iter = a.grids[Bg->grid].start_iter;
+        U.emu = (sizeof(T) == 8 && a.emu && a.norms && a.norms[Bg->grid].emu_bad == 0u) ? 1 : 0;
+      }
+    }
+  }
+  const int64_t it0 = a.it0_dev ? *a.it0_dev : a.it0;
+  Ring ring = ring_setup(smem, a.stages);  // ends with a CTA barrier
   for (int64_t t = 0; t < a.n_iters; ++t) {
-    const int64_t it = a.it0 + t;
-    for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
-      const int u = a.unit_ids[ui];
-      const int q0 = a.unit_items[ui], q1 = a.unit_items[ui + 1];
-      const BlockDev& B = a.blocks[a.items[q0].block];
-      if (t > 0) {
+    const int64_t it = it0 + t;
+    for (int k = 0; k < mine; ++k) {
+      const int ui = (int)blockIdx.x + k * G;
+      const BlockDev* Bp;
+      int u, q0, q1, ndep;
+      int64_t start;
+      bool emu;
+      if (cached) {
+        const UnitCache& U = s_u[k];
+        Bp = &U.B;
+        u = U.unit;
+        q0 = U.q0;
+        q1 = U.q1;
+        ndep = U.ndep;
+        start = U.start_iter;
+        emu = U.emu != 0;
+      } else {
+        q0 = a.unit_items[ui];
+        q1 = a.unit_items[ui + 1];
+        u = a.unit_ids[ui];
+        Bp = &a.blocks[a.items[q0].block];
+        ndep = a.dep_off[ui + 1] - a.dep_off[ui];
+        start = a.grids[Bp->grid].start_iter;
+        emu = sizeof(T) == 8 && a.emu && a.norms && a.norms[Bp->grid].emu_bad == 0u;
+      }
+      if (t > 0 && tid < 32) {
         // One lane per partner: the flags are polled in parallel, so the wait
         // costs one round trip instead of one per partner (same-box A/B: 64^3
         // FP64 in 2x2x2 blocks 22.0 -> 24.3 GLUP/s, 256-grid FP32 batch
         // 109.5 -> 114.0).
-        if (tid < 32) {
-          bool okw = true;
-          for (int d = a.dep_off[ui] + tid; d < a.dep_off[ui + 1] && okw; d += 32)
-            okw = wait_ge(a.progress + a.dep_ids[d], it, a.err, a.wait_ns);
-          okw = __all_sync(0xffffffffu, okw);
-          __syncwarp();
-          if (tid == 0) {
-            fence_proxy_async();
-            s_ok = okw ? 1 : 0;
-          }
+        bool okw = true;
+        for (int d = lane; d < ndep && okw; d += 32) {
+          const int dep = (cached && ndep <= kPersistDeps) ? s_u[k].dep[d] : a.dep_ids[a.dep_off[ui] + d];
+          okw = wait_ge(a.progress + dep, it, a.err, a.wait_ns);
         }
-        __syncthreads();
-        if (!s_ok) return;
+        okw = __all_sync(0xffffffffu, okw);
+        if (tid == 0) {
+          fence_proxy_async();
+          s_ok = okw ? 1 : 0;
+        }
       }
-      const int p = (int)((it - a.grids[B.grid].start_iter) & 1);
+      const int p = (int)((it - start) & 1);
+      if (tid < 6) s_tab[tid] = cached ? s_u[k].send[p ^ 1][tid] : Bp->send[tid][p ^ 1];
+      __syncthreads();
+      if (t > 0 && !s_ok) return;
       const bool resid = a.resid_first && t == 0;
-      const bool emu = sizeof(T) == 8 && a.emu && a.norms && a.norms[B.grid].emu_bad == 0u;
       for (int q = q0; q < q1; ++q) {
         const WorkItem w = a.items[q];
         bool ok;
         if (resid) {
-          const double acc = run_item<T, kWrite | kPack | kResid>(B, p, w, ring, a.err, a.wait_ns, emu, ok);
+          const double acc = run_item<T, kWrite | kPack | kResid>(*Bp, p, w, ring, a.err, a.wait_ns, emu, ok, s_tab);
           const double s = block_sum<kThreads>(acc, red);
           if (tid == 0) a.partials[w.slot] = s;
         } else {
-          run_item<T, kWrite | kPack>(B, p, w, ring, a.err, a.wait_ns, emu, ok);
+          run_item<T, kWrite | kPack>(*Bp, p, w, ring, a.err, a.wait_ns, emu, ok, s_tab);
         }
         if (!ok) return;  // CTA-uniform
       }
       fence_proxy_async();
       __syncthreads();
-      if (tid == 0) {
-        __threadfence();
-        st_release(a.progress + u, it + 1);
-      }
+      if (tid == 0) st_release(a.progress + u, it + 1);
     }
   }
 }

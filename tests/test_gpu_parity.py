@@ -180,6 +180,24 @@ def test_ragged_block_shapes(oracle_mod, dtype, path):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_persistent_replays_continue(oracle_mod, dtype):
+    """The persistent path captures its cooperative launch once per launch
+    shape and replays it, reading the start iteration from device memory:
+    calls of the same and of different lengths continue where the last one
+    stopped, bit-exact with the oracle."""
+    grid, split = (45, 37, 29), ("count", (3, 5, 7))
+    init = dict(bc="uniform", bc_seed=23, interior="uniform", interior_seed=24)
+    npdt = np.float64 if dtype == "f64" else np.float32
+    u0 = J.initial_grid(*grid, dtype=npdt, **init)
+    with _solver(grid, split, dtype, init, "persistent") as s:
+        for n in (7, 7, 7, 5, 7):
+            s.step(n)
+        s.sync()
+        got = s.copy_out()
+    assert np.array_equal(got, J.interior_of(oracle_mod.jacobi(u0, 33)))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_residual_parity(oracle_mod, dtype):
     grid = (37, 29, 41)
     init = dict(bc="linear_noise", bc_seed=7, noise_amp=1e-3, interior="uniform", interior_seed=8)
@@ -334,6 +352,23 @@ def test_config2_full_size_vs_oracle(oracle_mod):
     assert np.array_equal(got, J.interior_of(want))
 
 
+def test_weak_scaling_slab_full_size_vs_oracle(oracle_mod):
+    """One GPU's share of the paper's weak-scaling base problem (1536^3 points
+    per node of six GPUs, Sec. 4.3): 1536 x 768 x 512 FP64 in 64^3 blocks,
+    the benchmark's launch configuration, 24 iterations bit-exact with the
+    oracle (the front from the boundary reaches 24 points in)."""
+    w = J.WORKLOADS["jacobi3d-fp64-1536x768x512"]
+    init = dict(bc=w["bc"], bc_seed=w["bc_seed"], interior=w["interior"], interior_seed=w["interior_seed"])
+    u0 = J.initial_grid(*w["grid"], **init)
+    with _solver(w["grid"], w["split"], "f64", init, "graph") as s:
+        assert set(s.kind_items()) == {"stream8"}
+        s.step(24)
+        got = s.copy_out()
+    want = oracle_mod.jacobi(u0, 24)
+    del u0
+    assert np.array_equal(got, J.interior_of(want))
+
+
 def test_config2_invariance_1000_iters():
     """1000 iterations: 8x8x8 blocks equal 2x2x2 blocks bit for bit."""
     w, init = _cfg2()
@@ -480,22 +515,60 @@ def test_batched_full_size(oracle_mod, name):
 
 
 def test_autotune_keeps_results(tmp_path, monkeypatch, oracle_mod):
+    """The autotuner times shapes x paths (and ring depths) on a scratch handle,
+    applies the winner and caches it; the tuned handle's iterates equal the
+    oracle's."""
     monkeypatch.setenv("JACOBI_TUNE_CACHE", str(tmp_path / "tune.txt"))
     grids, splits, inits, dtype, _ = _batched("jacobi3d-batched256-fp32")
     grids, splits, inits = grids[:12], splits[:12], inits[:12]
     with jg.Jacobi3D(grids, splits, dtype, inits) as s:
         r = s.autotune(8)
-        assert r["n_tried"] >= 3 and not r["from_cache"] and r["ms_per_iter"] > 0
-        assert jg.PATH_NAMES[s.info.path] == r["path"] and s.info.stages == r["stages"]
+        assert r["n_tried"] >= 6 and not r["from_cache"] and r["ms_per_iter"] > 0
+        info = s.info
+        assert jg.PATH_NAMES[info.path] == r["path"] and info.stages == r["stages"]
+        assert (info.zchunk, info.cw_cap) == (r["zchunk"], r["cw_cap"])
         s.step(17)
         s.sync()
         tuned = [s.copy_out(g) for g in range(len(grids))]
     with jg.Jacobi3D(grids, splits, dtype, inits) as s:
         r2 = s.autotune(8)
-        assert r2["from_cache"] and (r2["path"], r2["stages"]) == (r["path"], r["stages"])
+        assert r2["from_cache"]
+        assert (r2["path"], r2["stages"], r2["zchunk"], r2["cw_cap"]) == (r["path"], r["stages"], r["zchunk"],
+                                                                        r["cw_cap"])
     for g in (0, 5, 11):
         want = oracle_mod.jacobi(J.initial_grid(*grids[g], dtype=np.float32, **inits[g]), 17)
         assert np.array_equal(tuned[g], J.interior_of(want))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_shapes_give_identical_iterates(oracle_mod, dtype):
+    """Every work-item shape (z-chunk depth, consumer-warp cap) on the graph
+    and persistent paths gives the oracle's iterates on uneven grids with
+    ragged blocks and 64-wide planes; a shape finer than the tables hold is
+    refused."""
+    grids = [(70, 64, 37), (45, 37, 29), (33, 18, 50)]
+    splits = [("shape", (64, 64, 64)), ("count", (3, 5, 2)), ("shape", (11, 9, 16))]
+    inits = [dict(bc="uniform", bc_seed=81 + g, interior="uniform", interior_seed=91 + g) for g in range(3)]
+    npdt = np.float64 if dtype == "f64" else np.float32
+    want = [J.interior_of(oracle_mod.jacobi(J.initial_grid(*grids[g], dtype=npdt, **inits[g]), 11))
+            for g in range(3)]
+    with jg.Jacobi3D(grids, splits, dtype, inits) as s0:
+        zc0 = s0.info.zchunk
+    for path in ("graph", "persistent"):
+        for zc, cw in ((zc0, 8), (zc0, 2), (max(1, zc0 // 2), 4), (max(1, zc0 // 4), 2), (2 * zc0, 8)):
+            with jg.Jacobi3D(grids, splits, dtype, inits, path=path) as s:
+                s.set_shape(zc, cw)
+                assert (s.info.zchunk, s.info.cw_cap) == (min(zc, 37), cw)  # 37: the tallest block
+                s.step(5)
+                s.step(6)
+                s.sync()
+                for g in range(3):
+                    assert np.array_equal(s.copy_out(g), want[g]), (path, zc, cw, g)
+    with jg.Jacobi3D(grids, splits, dtype, inits) as s:
+        if zc0 >= 8:
+            with pytest.raises(jg.JacobiError) as e:
+                s.set_shape(1, 2)
+            assert e.value.code == jg.JACOBI_EINVAL
 
 
 # ---- failure detection: bounded waits, no hang ----------------------------------

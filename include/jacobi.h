@@ -209,7 +209,7 @@ typedef struct {
   int32_t n_tried;       /* candidates timed (0 when taken from the cache)      */
   int32_t from_cache;
   int64_t zchunk;        /* chosen z-chunk depth (planes per work item)         */
-  int32_t cw_cap;        /* chosen consumer-warp cap per streaming CTA (2/4/8)  */
+  int32_t cw_cap;        /* chosen consumer-warp cap per streaming CTA (2/4/8; 0 = tiles) */
   int32_t pad_;
 } jacobi_tune_result;
 
@@ -274,19 +274,21 @@ int jacobi_set_path(jacobi_t* h, int32_t path);
  * the library's cost model; clamped to the tallest block).  cw_cap: at most 2,
  * 4 or 8 consumer warps per plane-streaming CTA; a CTA of CW warps covers
  * 4 * 32 * CW / (row vectors) rows of a plane, so a lower cap cuts planes into
- * more, shorter row windows (a row's vectors always fit one CTA).  Iterates do
- * not depend on the shape (bit for bit); residual sums are reproducible for a
- * given shape.  The item tables hold the finest shape down to a quarter of
- * the planned z-chunk and 2 warps: finer ones give JACOBI_EINVAL.
- * Synchronises the stream. */
+ * more, shorter row windows (a row's vectors always fit one CTA); 0 sends
+ * every block to the tile kernel (32 x 8 columns per CTA, plain loads, no
+ * bulk-copy ring).  Iterates do not depend on the shape (bit for bit);
+ * residual sums are reproducible for a given shape.  The item tables hold the
+ * finest shapes down to a quarter of the planned z-chunk: finer ones give
+ * JACOBI_EINVAL.  Synchronises the stream. */
 int jacobi_set_shape(jacobi_t* h, int64_t zchunk, int32_t cw_cap, void* stream);
 
 /* Autotuner (the library's addition): times candidate step configurations
- * for iters_per_trial iterations on a scratch handle with the same grids,
+ * (each for at least iters_per_trial iterations and ~2 ms, best of two runs)
+ * on a scratch handle with the same grids,
  * splits and dtype (the handle's own state is untouched): every shape of
  * jacobi_set_shape with a z-chunk of 2, 1, 1/2 or 1/4 times the cost model's
- * and a warp cap of 8, 4 or 2 (shapes that give the same items are timed
- * once), each on the GRAPH path and the PERSISTENT kernel; then FUSED and the
+ * and a warp cap of 8, 4, 2 or 0 (tiles; shapes that give the same items are
+ * timed once), each on the GRAPH path and the PERSISTENT kernel; then FUSED and the
  * persistent ring depths 3..6 at the best shape.  Applies the fastest (path,
  * ring depth, shape) to `h`.  All candidates give bit-identical iterates.
  * When the environment variable JACOBI_TUNE_CACHE names a file, results are

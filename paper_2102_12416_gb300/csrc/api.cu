@@ -168,7 +168,7 @@ int plan_items(Plan* P, int64_t zc_req, int cw_cap, int64_t target_items, int64_
     BlockHost& B = P->blocks[b];
     uint32_t sb = 0;
     int64_t ch = 0;
-    const int cw = stream_shape(B.rx, B.ry, P->elem, cw_cap, &sb, &ch);
+    const int cw = cw_cap > 0 ? stream_shape(B.rx, B.ry, P->elem, cw_cap, &sb, &ch) : 0;  // 0: tiles
     warps[b] = cw;
     chunks[b] = ch;
     if (cw) P->max_stage = std::max(P->max_stage, sb);
@@ -302,18 +302,20 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
   }
   int rc = plan_items(P, 0, 8, target_items, min_chunk);
   if (rc) return rc;
-  // Table capacity: the item and unit tables are sized for the finest shape
+  // Table capacity: the item and unit tables are sized for the finest shapes
   // jacobi_set_shape accepts and the autotuner tries (z-chunks down to a
-  // quarter of the planned one, CTAs down to 2 consumer warps), so a handle
-  // can be re-planned in place; states and slots never move.
+  // quarter of the planned one, CTAs down to 2 consumer warps, or tiles), so a
+  // handle can be re-planned in place; states and slots never move.
   P->cap_items = (int64_t)P->items.size();
   P->cap_units = P->n_units;
   if (target_items <= 0) {
-    Plan probe = *P;
-    rc = plan_items(&probe, std::max<int64_t>(1, P->zchunk / 4), 2, 0, 1);
-    if (rc) return rc;
-    P->cap_items = std::max(P->cap_items, (int64_t)probe.items.size());
-    P->cap_units = std::max(P->cap_units, probe.n_units);
+    for (int cw : {2, 0}) {
+      Plan probe = *P;
+      rc = plan_items(&probe, std::max<int64_t>(1, P->zchunk / 4), cw, 0, 1);
+      if (rc) return rc;
+      P->cap_items = std::max(P->cap_items, (int64_t)probe.items.size());
+      P->cap_units = std::max(P->cap_units, probe.n_units);
+    }
   }
   if (P->cap_items > (1ll << 30)) return set_error(JACOBI_EINVAL, "too many work items");
   const int64_t nb = (int64_t)P->blocks.size(), ni = P->cap_items, ng = n_grids;
@@ -622,7 +624,8 @@ int step_graph(jacobi_t* h, int64_t it0, int64_t n, cudaStream_t s) {
 
 int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaStream_t s) {
   const int smem = 128 + h->stages * (int32_t)h->plan.max_stage;
-  const int maxc = persistent_max_ctas(h->plan.dtype, smem);
+  const int threads = persistent_threads(h->active_items.data(), h->active_items.size());
+  const int maxc = persistent_max_ctas(h->plan.dtype, smem, threads);
   if (maxc <= 0) return set_error(JACOBI_ECUDA, "occupancy query for the persistent kernel failed");
   PersistLaunch a;
   a.blocks = h->d_blocks;
@@ -646,14 +649,14 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
   a.smem = smem;
   a.norms = h->d_norms;
   a.emu = h->fp64_emu;
-  a.pad_ = 0;
+  a.threads = threads;
   const int ctas = std::min(maxc, a.n_units);
   // Replay a captured graph of the same launch shape; the start iteration
   // goes to device memory first (a pageable source is staged before the call
   // returns, so the stack variable may go).
   jacobi_s::PersistGraph& pg = h->pgraph[resid_first ? 1 : 0];
   if (!h->pgraph_off && (!pg.exec || pg.n_iters != n || pg.n_units != a.n_units || pg.stages != a.stages ||
-                         pg.ctas != ctas)) {
+                         pg.ctas != ctas || pg.threads != threads)) {
     if (pg.exec) cudaGraphExecDestroy(pg.exec);
     pg.exec = nullptr;
     PersistLaunch c = a;
@@ -695,6 +698,7 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
       pg.n_units = a.n_units;
       pg.stages = a.stages;
       pg.ctas = ctas;
+      pg.threads = threads;
     }
   }
   if (!h->pgraph_off && pg.exec) {
@@ -924,7 +928,7 @@ void activate_grid(jacobi_t* h, int64_t g) {
 // were sized for the finest accepted shape).  Recomputes |b| (its summation
 // order follows the items) and drops captured graphs.
 int apply_shape(jacobi_t* h, int64_t zchunk, int32_t cw_cap, cudaStream_t s) {
-  if (zchunk < 0 || (cw_cap != 2 && cw_cap != 4 && cw_cap != 8))
+  if (zchunk < 0 || (cw_cap != 0 && cw_cap != 2 && cw_cap != 4 && cw_cap != 8))
     return set_error(JACOBI_EINVAL, "bad shape: zchunk %lld, cw_cap %d", (long long)zchunk, cw_cap);
   Plan Q = h->plan;
   int rc = plan_items(&Q, zchunk, cw_cap, 0, 1);
@@ -1264,7 +1268,7 @@ extern "C" int jacobi_autotune(jacobi_t* h, int64_t iters_per_trial, void* strea
     std::vector<std::pair<int64_t, int32_t>> shapes;
     std::vector<std::vector<WorkItem>> seen;
     for (int64_t zc : {zc0, 2 * zc0, std::max<int64_t>(1, zc0 / 2), std::max<int64_t>(1, zc0 / 4)})
-      for (int32_t cw : {8, 4, 2}) {
+      for (int32_t cw : {8, 4, 2, 0}) {
         Plan q = t->plan;
         if (plan_items(&q, zc, cw, 0, 1) || (int64_t)q.items.size() > q.cap_items || q.n_units > q.cap_units) continue;
         bool dup = false;
@@ -1278,22 +1282,40 @@ extern "C" int jacobi_autotune(jacobi_t* h, int64_t iters_per_trial, void* strea
         seen.push_back(q.items);
         shapes.push_back({zc, cw});
       }
+    // One timed run of n iterations (ms per iteration), after the warm-up.
+    auto timed = [&](int64_t n, double* per) -> int {
+      int rc2 = JACOBI_OK;
+      if (cudaEventRecord(e0, s) != cudaSuccess) rc2 = JACOBI_ECUDA;
+      if (!rc2) rc2 = do_step(t, n, s);
+      if (!rc2 && cudaEventRecord(e1, s) != cudaSuccess) rc2 = JACOBI_ECUDA;
+      if (!rc2 && cudaEventSynchronize(e1) != cudaSuccess) rc2 = JACOBI_ECUDA;
+      if (!rc2) rc2 = check_err_word(t, s);
+      float ms = 0.f;
+      if (!rc2) cudaEventElapsedTime(&ms, e0, e1);
+      *per = ms / (double)n;
+      return rc2;
+    };
+    // A trial runs at least iters_per_trial iterations and at least ~2 ms (a
+    // short problem's iteration takes microseconds, too short to rank
+    // candidates from one run), best of two runs.
     auto trial = [&](int32_t path, int32_t st, int64_t zc, int32_t cw) -> int {
       int rc2 = apply_shape(t, zc, cw, s);
       if (rc2) return rc2;
       t->stages = st;
       t->path = path;
       t->tables_dirty = true;
-      rc2 = do_step(t, std::max<int64_t>(iters_per_trial / 4, 2), s);  // warm-up (graph capture etc.)
-      if (!rc2 && cudaEventRecord(e0, s) != cudaSuccess) rc2 = JACOBI_ECUDA;
-      if (!rc2) rc2 = do_step(t, iters_per_trial, s);
-      if (!rc2 && cudaEventRecord(e1, s) != cudaSuccess) rc2 = JACOBI_ECUDA;
-      if (!rc2 && cudaEventSynchronize(e1) != cudaSuccess) rc2 = JACOBI_ECUDA;
-      if (!rc2) rc2 = check_err_word(t, s);
+      double est = 0.0;
+      rc2 = timed(std::max<int64_t>(iters_per_trial / 4, 2), &est);  // warm-up (graph capture etc.)
       if (rc2) return rc2;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      const double per = ms / (double)iters_per_trial;
+      const int64_t n = std::min<int64_t>(std::max<int64_t>(iters_per_trial, (int64_t)std::ceil(2.0 / std::max(est, 1e-4))),
+                                          50 * iters_per_trial);
+      double per = INFINITY;
+      for (int rep = 0; rep < 2 && !rc2; ++rep) {
+        double p1 = 0.0;
+        rc2 = timed(n, &p1);
+        per = std::min(per, p1);
+      }
+      if (rc2) return rc2;
       r.n_tried += 1;
       if (per < best) {
         best = per;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace jgb {
@@ -155,9 +157,16 @@ struct PersistLaunch {
   int32_t smem;
   const GridNorm* norms;       // per-grid emu_bad flags (FP64 only)
   int32_t emu;
-  int32_t pad_;
+  int32_t threads;             // CTA size: 64, 128 or 256 (see persistent_threads)
 };
 cudaError_t launch_persistent(const PersistLaunch& a, int grid_ctas, cudaStream_t s);
-int persistent_max_ctas(int dtype, int smem);  // co-resident CTA limit (0 on error)
+int persistent_max_ctas(int dtype, int smem, int threads);  // co-resident CTA limit (0 on error)
+// Smallest persistent CTA (64, 128, 256 threads) that covers every item:
+// 32 * CW threads for streamed items of CW consumer warps, 256 for tiles.
+inline int persistent_threads(const WorkItem* items, size_t n) {
+  int t = 64;
+  for (size_t i = 0; i < n; ++i) t = std::max(t, items[i].x0 >= 0 ? 256 : 32 * (items[i].y0 & 15));
+  return t;
+}
 
 }  // namespace jgb

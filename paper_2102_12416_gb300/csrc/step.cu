@@ -722,10 +722,15 @@ struct UnitCache {
 static_assert(kPersistCache * sizeof(UnitCache) + 512 <= 227 * 1024 - kMaxStepSmem,
               "the persistent kernel's static shared memory must fit beside the largest ring");
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_persist(PersistLaunch a) {
+// NT threads per CTA (64, 128 or 256): the host picks the smallest that
+// covers every streamed row window of the launch (a window of W rows and V
+// vector columns needs V * W / 4 threads), or 256 when tile items are present
+// (one TX x TY tile per CTA), so CTAs of small blocks keep every thread busy.
+// Registers are capped at 128 per thread.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_persist(PersistLaunch a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ double red[kThreads / 32];
+  __shared__ double red[NT / 32];
   __shared__ int s_ok;
   __shared__ UnitCache s_u[kPersistCache];
   __shared__ void* s_tab[6];
@@ -734,7 +739,7 @@ __global__ void __launch_bounds__(kThreads) k_persist(PersistLaunch a) {
   const int mine = a.n_units > (int)blockIdx.x ? (a.n_units - (int)blockIdx.x + G - 1) / G : 0;
   const bool cached = mine <= kPersistCache;
   if (cached) {
-    for (int k = tid >> 5; k < mine; k += kThreads / 32) {  // one warp per unit
+    for (int k = tid >> 5; k < mine; k += NT / 32) {  // one warp per unit
       const int ui = (int)blockIdx.x + k * G;
       UnitCache& U = s_u[k];
       const int q0 = a.unit_items[ui];
@@ -809,7 +814,7 @@ __global__ void __launch_bounds__(kThreads) k_persist(PersistLaunch a) {
         bool ok;
         if (resid) {
           const double acc = run_item<T, kWrite | kPack | kResid>(*Bp, p, w, ring, a.err, a.wait_ns, emu, ok, s_tab);
-          const double s = block_sum<kThreads>(acc, red);
+          const double s = block_sum<NT>(acc, red);
           if (tid == 0) a.partials[w.slot] = s;
         } else {
           run_item<T, kWrite | kPack>(*Bp, p, w, ring, a.err, a.wait_ns, emu, ok, s_tab);
@@ -896,15 +901,25 @@ cudaError_t launch_step_t(const StepLaunch& a, int mode, cudaStream_t s, const K
   }
 }
 
-template <typename T>
-const void* persist_fn() {
+template <typename T, int NT>
+const void* persist_fn_t() {
   static bool attr_set = false;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(k_persist<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxStepSmem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_persist<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxStepSmem) !=
+        cudaSuccess)
       return nullptr;
     attr_set = true;
   }
-  return (const void*)k_persist<T>;
+  return (const void*)k_persist<T, NT>;
+}
+
+const void* persist_fn(int dtype, int threads) {
+  if (dtype == 0) {
+    return threads == 64 ? persist_fn_t<double, 64>() : threads == 128 ? persist_fn_t<double, 128>()
+                                                                       : persist_fn_t<double, 256>();
+  }
+  return threads == 64 ? persist_fn_t<float, 64>() : threads == 128 ? persist_fn_t<float, 128>()
+                                                                    : persist_fn_t<float, 256>();
 }
 
 }  // namespace
@@ -934,13 +949,13 @@ void kind_fork_destroy(KindFork* f) {
   }
 }
 
-int persistent_max_ctas(int dtype, int smem) {
+int persistent_max_ctas(int dtype, int smem, int threads) {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  const void* fn = dtype == 0 ? persist_fn<double>() : persist_fn<float>();
+  const void* fn = persist_fn(dtype, threads);
   if (!fn) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess) return 0;
   return per_sm * sms;
 }
 
@@ -948,9 +963,9 @@ cudaError_t launch_persistent(const PersistLaunch& a, int grid_ctas, cudaStream_
   if (a.n_units <= 0 || a.n_iters <= 0) return cudaSuccess;
   PersistLaunch args = a;
   void* params[] = {&args};
-  const void* fn = a.dtype == 0 ? persist_fn<double>() : persist_fn<float>();
+  const void* fn = persist_fn(a.dtype, a.threads);
   if (!fn) return cudaErrorInvalidValue;
-  return cudaLaunchCooperativeKernel(fn, dim3(grid_ctas), dim3(kThreads), params, a.smem, s);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid_ctas), dim3(a.threads), params, a.smem, s);
 }
 
 }  // namespace jgb

@@ -555,7 +555,8 @@ def test_shapes_give_identical_iterates(oracle_mod, dtype):
     with jg.Jacobi3D(grids, splits, dtype, inits) as s0:
         zc0 = s0.info.zchunk
     for path in ("graph", "persistent"):
-        for zc, cw in ((zc0, 8), (zc0, 2), (max(1, zc0 // 2), 4), (max(1, zc0 // 4), 2), (2 * zc0, 8)):
+        for zc, cw in ((zc0, 8), (zc0, 2), (max(1, zc0 // 2), 4), (max(1, zc0 // 4), 2), (2 * zc0, 8),
+                       (zc0, 0), (max(1, zc0 // 4), 0)):
             with jg.Jacobi3D(grids, splits, dtype, inits, path=path) as s:
                 s.set_shape(zc, cw)
                 assert (s.info.zchunk, s.info.cw_cap) == (min(zc, 37), cw)  # 37: the tallest block

@@ -31,6 +31,9 @@
  *   JACOBI_FP64_EMU=0  keeps every FP64 add on the FP64 pipe (see
  *                      jacobi_selftest_dadd);
  *   JACOBI_STAGES      ring depth (3..8) of the persistent kernel;
+ *   JACOBI_PERSIST_WS=0  keeps the persistent path on its barrier-driven
+ *                      kernel (by default launches whose items are all
+ *                      plane-streamed run the warp-specialised one);
  *   JACOBI_TUNE_CACHE  file that caches jacobi_autotune's choices.
  *
  * Data layout of a grid of nx*ny*nz interior points ("interior" layout): one

@@ -625,8 +625,35 @@ int step_graph(jacobi_t* h, int64_t it0, int64_t n, cudaStream_t s) {
 int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaStream_t s) {
   const int smem = 128 + h->stages * (int32_t)h->plan.max_stage;
   const int threads = persistent_threads(h->active_items.data(), h->active_items.size());
-  const int maxc = persistent_max_ctas(h->plan.dtype, smem, threads);
+  // The warp-specialised kernel takes launches whose items are all streamed
+  // (no tiles), whose units have at most 8 partners and whose CTAs own at most
+  // kPersistCache units each; the barrier-driven kernel takes the others.
+  int ws_cw = 0, maxc = 0;
+  if (h->persist_ws) {
+    bool tiles = false;
+    int cw = 2;
+    for (const WorkItem& w : h->active_items) {
+      tiles = tiles || w.x0 >= 0;
+      cw = std::max(cw, (int)(w.y0 & 15));
+    }
+    int maxdep = 0;
+    for (size_t u = 0; u + 1 < h->active_dep_off.size(); ++u)
+      maxdep = std::max(maxdep, h->active_dep_off[u + 1] - h->active_dep_off[u]);
+    if (!tiles && maxdep <= 8 && !h->active_units.empty()) {
+      const int m = persistent_max_ctas(h->plan.dtype, smem, 0, cw);
+      const int64_t nu = (int64_t)h->active_units.size();
+      if (m > 0 && (nu + std::min<int64_t>(m, nu) - 1) / std::min<int64_t>(m, nu) <= kPersistCache) {
+        ws_cw = cw;
+        maxc = m;
+      }
+    }
+  }
+  if (!ws_cw) maxc = persistent_max_ctas(h->plan.dtype, smem, threads);
   if (maxc <= 0) return set_error(JACOBI_ECUDA, "occupancy query for the persistent kernel failed");
+  if (ws_cw && resid_first && n > 1) {  // its residual launches run one iteration
+    int rc = step_persistent(h, it0, 1, true, s);
+    return rc ? rc : step_persistent(h, it0 + 1, n - 1, false, s);
+  }
   PersistLaunch a;
   a.blocks = h->d_blocks;
   a.items = h->d_active;
@@ -650,13 +677,15 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
   a.norms = h->d_norms;
   a.emu = h->fp64_emu;
   a.threads = threads;
+  a.ws_cw = ws_cw;
+  a.stage_bytes = (int32_t)h->plan.max_stage;
   const int ctas = std::min(maxc, a.n_units);
   // Replay a captured graph of the same launch shape; the start iteration
   // goes to device memory first (a pageable source is staged before the call
   // returns, so the stack variable may go).
   jacobi_s::PersistGraph& pg = h->pgraph[resid_first ? 1 : 0];
   if (!h->pgraph_off && (!pg.exec || pg.n_iters != n || pg.n_units != a.n_units || pg.stages != a.stages ||
-                         pg.ctas != ctas || pg.threads != threads)) {
+                         pg.ctas != ctas || pg.threads != threads || pg.ws_cw != ws_cw)) {
     if (pg.exec) cudaGraphExecDestroy(pg.exec);
     pg.exec = nullptr;
     PersistLaunch c = a;
@@ -699,6 +728,7 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
       pg.stages = a.stages;
       pg.ctas = ctas;
       pg.threads = threads;
+      pg.ws_cw = ws_cw;
     }
   }
   if (!h->pgraph_off && pg.exec) {
@@ -1109,6 +1139,7 @@ int jacobi_create_batch(int64_t n_grids, const jacobi_dim3* grids, const jacobi_
   // pick another); the per-step kernels always use kStreamStages.
   h->stages = 4;
   if (const char* em = getenv("JACOBI_FP64_EMU")) h->fp64_emu = atoi(em) != 0 ? 1 : 0;
+  if (const char* pw = getenv("JACOBI_PERSIST_WS")) h->persist_ws = atoi(pw) != 0;
   if (const char* st = getenv("JACOBI_STAGES")) {
     const int v = atoi(st);
     if (v >= 3 && v <= 8) h->stages = v;

@@ -168,7 +168,8 @@ __global__ void k_gather(const BlockDev* __restrict__ blocks, const BlockGeom* _
 
 // |b|^2 partials: the residual expression with every interior value set to 0,
 // so only Dirichlet ghosts contribute.  A work item is either one TX x TY tile
-// (x0 >= 0) or a whole x-y plane range of its block (x0 < 0).
+// (x0 >= 0) or the row window [ya, yb) of its block's planes over [z0, z1)
+// (x0 < 0; a plane may be split into several windows, each its own item).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_bnorm(StepLaunch a) {
   const WorkItem w = a.items[blockIdx.x];
@@ -176,13 +177,13 @@ __global__ void __launch_bounds__(kThreads) k_bnorm(StepLaunch a) {
   const int p = (int)((a.it - a.grids[B.grid].start_iter) & 1);
   const int nx = B.nx, ny = B.ny, nz = B.nz, rx = B.rx, ry = B.ry;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int xa = w.x0 >= 0 ? w.x0 : 0, ya = w.x0 >= 0 ? w.y0 : 0;
-  const int xb = w.x0 >= 0 ? w.x0 + TX : nx, yb = w.x0 >= 0 ? w.y0 + TY : ny;
+  const int xa = w.x0 >= 0 ? w.x0 : 0, ya = w.x0 >= 0 ? w.y0 : w.ya;
+  const int xb = w.x0 >= 0 ? w.x0 + TX : nx, yb = min(w.x0 >= 0 ? w.y0 + TY : (int)w.yb, ny);
   double acc = 0.0;
   for (int y0 = ya; y0 < yb; y0 += TY)
     for (int x0 = xa; x0 < xb; x0 += TX) {
       const int i = x0 + tx, j = y0 + ty;
-      if (i >= nx || j >= ny) continue;
+      if (i >= nx || j >= yb) continue;
       for (int k = w.z0; k < w.z1; ++k) {
         double v[6] = {0, 0, 0, 0, 0, 0};
         if (i == 0 && B.nbr[XM] < 0) v[0] = (double)((const T*)B.recv[XM][p])[(int64_t)k * ry + j];

@@ -26,8 +26,11 @@ struct BlockGeom {
 
 // Largest dynamic shared memory a step kernel may use (sm_103a opt-in limit of
 // 227 KB per CTA, minus room for the kernels' static shared memory: the
-// persistent kernel keeps its units' tables there, about 3.5 KB).
-constexpr int kMaxStepSmem = 227 * 1024 - 4096;
+// persistent kernels keep up to 32 units' tables there, about 13.6 KB).
+constexpr int kMaxStepSmem = 227 * 1024 - 16384;
+// Units per CTA whose tables the persistent kernels cache in shared memory
+// (the warp-specialised one needs all of a CTA's units cached).
+constexpr int kPersistCache = 32;
 
 // A plane-streaming item encodes its consumer warps (2, 4 or 8) in the low
 // bits of y0 and, in bit 4, whether its block has padding (ragged rows or
@@ -157,10 +160,13 @@ struct PersistLaunch {
   int32_t smem;
   const GridNorm* norms;       // per-grid emu_bad flags (FP64 only)
   int32_t emu;
-  int32_t threads;             // CTA size: 64, 128 or 256 (see persistent_threads)
+  int32_t threads;             // barrier-driven kernel: CTA size 64, 128 or 256 (persistent_threads)
+  int32_t ws_cw;               // > 0: the warp-specialised kernel with this many consumer warps
+  int32_t stage_bytes;         // ring stage stride of the warp-specialised kernel (largest stage)
 };
 cudaError_t launch_persistent(const PersistLaunch& a, int grid_ctas, cudaStream_t s);
-int persistent_max_ctas(int dtype, int smem, int threads);  // co-resident CTA limit (0 on error)
+// Co-resident CTA limit of the persistent kernel for (threads, ws_cw) (0 on error).
+int persistent_max_ctas(int dtype, int smem, int threads, int ws_cw = 0);
 // Smallest persistent CTA (64, 128, 256 threads) that covers every item:
 // 32 * CW threads for streamed items of CW consumer warps, 256 for tiles.
 inline int persistent_threads(const WorkItem* items, size_t n) {

@@ -707,7 +707,6 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, StreamShape<CW>::min
 // store after the CTA barrier is cumulative, so it publishes every thread's
 // stores without a separate fence.
 // ---------------------------------------------------------------------------
-constexpr int kPersistCache = 8;
 constexpr int kPersistDeps = 8;  // a unit has at most 6 partners
 
 struct UnitCache {
@@ -828,6 +827,198 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_persist(PersistLaunc
   }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised persistent kernel (all items plane-streamed, every unit of
+// the CTA cached): CW consumer warps and one producer warp per CTA, as in
+// k_stream, but the ring of S stages (stride: the largest stage) runs on
+// across items, units and iterations.  The producer warp, for each unit in
+// turn, acquire-waits (bounded, one lane per flag) until the unit's partners
+// and the unit itself have finished the previous iteration, then its lane 0
+// streams the unit's planes into the ring, reusing a stage once every
+// consumer warp has released it; so it prefetches the next unit, or the next
+// iteration's first unit, while the consumers compute.  The consumers compute
+// each plane as k_stream does, release stages, and at the end of every item
+// meet on an mbarrier (bounded wait; no named barrier, which a warp leaving on
+// an error could hang): then one thread writes the item's residual partial
+// and, after a unit's last item, release-stores progress[u] = it + 1.  Every
+// thread fences its generic stores against the async proxy before that
+// meeting, since other CTAs' bulk copies read them.  Planes carry a global
+// sequence number g (stage g % S, phase (g / S) & 1) shared by both roles.
+// ---------------------------------------------------------------------------
+// RESID: the launch runs one iteration and fuses the residual of its state
+// (separate instantiations keep the plain sweep's register allocation).
+// Registers are capped at 96 per thread.
+template <typename T, int CW, bool RESID>
+__global__ void __launch_bounds__(StreamShape<CW>::threads, 65536 / (StreamShape<CW>::threads * 96))
+    k_persist_ws(PersistLaunch a) {
+  constexpr int VEC = V16<T>::N;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* full = (uint64_t*)smem;
+  uint64_t* empty = full + 8;
+  unsigned char* stages = smem + 128;
+  __shared__ UnitCache s_u[kPersistCache];
+  __shared__ uint64_t s_done;
+  __shared__ double s_red[2][CW];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int G = (int)gridDim.x, S = a.stages;
+  const size_t SB = (size_t)a.stage_bytes;
+  const int mine = a.n_units > (int)blockIdx.x ? (a.n_units - (int)blockIdx.x + G - 1) / G : 0;
+  if (mine > kPersistCache) {  // the host never launches this (CTA-uniform, before any barrier)
+    if (tid == 0) atomicCAS(a.err, (uint32_t)DEV_OK, (uint32_t)DEV_SEQ);
+    return;
+  }
+  for (int k = warp; k < mine; k += CW + 1) {  // one warp per unit
+    const int ui = (int)blockIdx.x + k * G;
+    UnitCache& U = s_u[k];
+    const int q0 = a.unit_items[ui];
+    const BlockDev* Bg = a.blocks + a.items[q0].block;
+    const uint32_t* src = (const uint32_t*)Bg;
+    uint32_t* dst = (uint32_t*)&U.B;
+    for (int i = lane; i < (int)(sizeof(BlockDev) / 4); i += 32) dst[i] = src[i];
+    if (lane < 12) U.send[lane / 6][lane % 6] = Bg->send[lane % 6][lane / 6];
+    const int d0 = a.dep_off[ui], d1 = a.dep_off[ui + 1];
+    if (lane < kPersistDeps) U.dep[lane] = d0 + lane < d1 ? a.dep_ids[d0 + lane] : 0;
+    if (lane == 0) {
+      U.unit = a.unit_ids[ui];
+      U.q0 = q0;
+      U.q1 = a.unit_items[ui + 1];
+      U.ndep = d1 - d0;
+      U.start_iter = a.grids[Bg->grid].start_iter;
+      U.emu = (sizeof(T) == 8 && a.emu && a.norms && a.norms[Bg->grid].emu_bad == 0u) ? 1 : 0;
+    }
+  }
+  if (tid == 0) {
+    for (int st = 0; st < S; ++st) {
+      mbar_init(full + st, 1);
+      mbar_init(empty + st, CW);
+    }
+    mbar_init(&s_done, CW);
+    mbar_fence_init();
+  }
+  const int64_t it0 = a.it0_dev ? *a.it0_dev : a.it0;
+  __syncthreads();
+  if (warp == CW) {
+    // ---- producer ----
+    int64_t g = 0;
+    bool ok = true;
+    for (int64_t t = 0; t < a.n_iters && ok; ++t) {
+      const int64_t it = it0 + t;
+      for (int k = 0; k < mine && ok; ++k) {
+        const UnitCache& U = s_u[k];
+        if (t > 0) {
+          bool okw = true;
+          if (lane < U.ndep) okw = wait_ge(a.progress + U.dep[lane], it, a.err, a.wait_ns);
+          else if (lane == U.ndep) okw = wait_ge(a.progress + U.unit, it, a.err, a.wait_ns);
+          ok = __all_sync(0xffffffffu, okw) != 0;
+          if (!ok) break;
+        }
+        if (lane == 0) {
+          fence_proxy_async();
+          const int p = (int)((it - U.start_iter) & 1);
+          for (int q = U.q0; q < U.q1 && ok; ++q) {
+            const WorkItem w = a.items[q];
+            const StageLayout L = stage_layout<T>(U.B, w.ya, w.yb);
+            const int nplanes = w.z1 - w.z0 + 2;
+            for (int j = 0; j < nplanes; ++j, ++g) {
+              const int st = (int)(g % S);
+              const int64_t fill = g / S;
+              if (fill > 0 && !mbar_ready(empty + st, (uint32_t)(fill - 1) & 1u, a.err, a.wait_ns)) {
+                ok = false;
+                break;
+              }
+              issue_plane<T>(U.B, p, w.z0, nplanes, j, w.ya, w.yb, L, stages + (size_t)st * SB, full + st);
+            }
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      }
+    }
+    if (!ok && lane == 0) {
+      // A wait expired: let the copies already issued land before leaving.
+      for (int st = 0; st < S; ++st) {
+        int64_t glast = -1;
+        for (int64_t x = st; x < g; x += S) glast = x;
+        if (glast >= 0) mbar_wait(full + st, (uint32_t)(glast / S) & 1u, a.err, a.wait_ns);
+      }
+    }
+    return;
+  }
+  // ---- consumers ----
+  int64_t g = 0, nitem = 0;
+  for (int64_t t = 0; t < a.n_iters; ++t) {
+    const int64_t it = it0 + t;
+    constexpr bool resid = RESID;
+    for (int k = 0; k < mine; ++k) {
+      const UnitCache& U = s_u[k];
+      const int p = (int)((it - U.start_iter) & 1);
+      PlaneView<T> O = plane_view<T>(U.B, p);
+      O.ss = U.send[p ^ 1];
+      const bool emu = U.emu != 0;
+      const int txv = O.rx / VEC;
+      for (int q = U.q0; q < U.q1; ++q, ++nitem) {
+        const WorkItem w = a.items[q];
+        const StageLayout L = stage_layout<T>(U.B, w.ya, w.yb);
+        const int nplanes = w.z1 - w.z0 + 2;
+        const bool rag = item_ragged(w);
+        const int tx = tid % txv, j0 = w.ya + (tid / txv) * 4;
+        const bool active = j0 < w.yb;
+        auto stage_of = [&](int64_t x) { return stages + (size_t)(x % S) * SB; };
+        auto ready = [&](int64_t x) {
+          return mbar_ready(full + (x % S), (uint32_t)(x / S) & 1u, a.err, a.wait_ns);
+        };
+        double acc = 0.0;
+        bool good = true;
+        for (int qq = 1; qq <= nplanes - 2 && good; ++qq) {
+          if (qq == 1) good = ready(g) && ready(g + 1);
+          good = good && ready(g + qq + 1);
+          good = __all_sync(0xffffffffu, good) != 0;
+          if (!good) break;
+          if (active) {
+            const unsigned char* sm = stage_of(g + qq - 1);
+            const unsigned char* sc = stage_of(g + qq);
+            const unsigned char* sp = stage_of(g + qq + 1);
+            const int kq = w.z0 - 1 + qq;
+            constexpr int MODE = RESID ? (kWrite | kPack | kResid) : (kWrite | kPack);
+            if (rag) {
+              if (sizeof(T) == 8 && emu) acc += stream_plane<T, 4, MODE, true, true, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+              else acc += stream_plane<T, 4, MODE, false, true, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+            } else {
+              if (sizeof(T) == 8 && emu) acc += stream_plane<T, 4, MODE, true, false, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+              else acc += stream_plane<T, 4, MODE, false, false, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+            }
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(empty + ((g + qq - 1) % S));
+        }
+        if (!good) return;  // the error word is set; the producer drains its copies
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(empty + ((g + nplanes - 2) % S));
+          mbar_arrive(empty + ((g + nplanes - 1) % S));
+        }
+        g += nplanes;
+        // item end: every consumer warp has stored its part
+        if (resid) {
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+          if (lane == 0) s_red[nitem & 1][warp] = acc;
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s_done);
+        if (!mbar_ready(&s_done, (uint32_t)(nitem & 1), a.err, a.wait_ns)) return;
+        if (tid == 0) {
+          if (resid) {
+            double r = 0.0;
+            for (int c = 0; c < CW; ++c) r += s_red[nitem & 1][c];
+            a.partials[w.slot] = r;
+          }
+          if (q == U.q1 - 1) st_release(a.progress + U.unit, it + 1);
+        }
+      }
+    }
+  }
+}
+
 template <typename K>
 cudaError_t set_smem_attr(K kernel, bool& done) {
   if (done) return cudaSuccess;
@@ -913,6 +1104,28 @@ const void* persist_fn_t() {
   return (const void*)k_persist<T, NT>;
 }
 
+template <typename T, int CW, bool R>
+const void* persist_ws_fn_t() {
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(k_persist_ws<T, CW, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxStepSmem) !=
+        cudaSuccess)
+      return nullptr;
+    attr_set = true;
+  }
+  return (const void*)k_persist_ws<T, CW, R>;
+}
+
+template <typename T, bool R>
+const void* persist_ws_fn_r(int cw) {
+  return cw == 2 ? persist_ws_fn_t<T, 2, R>() : cw == 4 ? persist_ws_fn_t<T, 4, R>() : persist_ws_fn_t<T, 8, R>();
+}
+
+const void* persist_ws_fn(int dtype, int cw, bool resid) {
+  if (dtype == 0) return resid ? persist_ws_fn_r<double, true>(cw) : persist_ws_fn_r<double, false>(cw);
+  return resid ? persist_ws_fn_r<float, true>(cw) : persist_ws_fn_r<float, false>(cw);
+}
+
 const void* persist_fn(int dtype, int threads) {
   if (dtype == 0) {
     return threads == 64 ? persist_fn_t<double, 64>() : threads == 128 ? persist_fn_t<double, 128>()
@@ -949,13 +1162,21 @@ void kind_fork_destroy(KindFork* f) {
   }
 }
 
-int persistent_max_ctas(int dtype, int smem, int threads) {
+int persistent_max_ctas(int dtype, int smem, int threads, int ws_cw) {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  const void* fn = persist_fn(dtype, threads);
+  const void* fn = ws_cw ? persist_ws_fn(dtype, ws_cw, false) : persist_fn(dtype, threads);
+  const int nt = ws_cw ? 32 * ws_cw + 32 : threads;
   if (!fn) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess) return 0;
+  if (ws_cw) {  // the residual instantiation must fit the same launch
+    int r = 0;
+    const void* fr = persist_ws_fn(dtype, ws_cw, true);
+    if (!fr || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, fr, nt, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem) != cudaSuccess) return 0;
+    return std::min(r, per_sm) * sms;
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem) != cudaSuccess) return 0;
   return per_sm * sms;
 }
 
@@ -963,9 +1184,12 @@ cudaError_t launch_persistent(const PersistLaunch& a, int grid_ctas, cudaStream_
   if (a.n_units <= 0 || a.n_iters <= 0) return cudaSuccess;
   PersistLaunch args = a;
   void* params[] = {&args};
-  const void* fn = persist_fn(a.dtype, a.threads);
+  // the warp-specialised kernel fuses the residual only in one-iteration launches
+  if (a.ws_cw && a.resid_first && a.n_iters != 1) return cudaErrorInvalidValue;
+  const void* fn = a.ws_cw ? persist_ws_fn(a.dtype, a.ws_cw, a.resid_first != 0) : persist_fn(a.dtype, a.threads);
+  const int nt = a.ws_cw ? 32 * a.ws_cw + 32 : a.threads;
   if (!fn) return cudaErrorInvalidValue;
-  return cudaLaunchCooperativeKernel(fn, dim3(grid_ctas), dim3(a.threads), params, a.smem, s);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid_ctas), dim3(nt), params, a.smem, s);
 }
 
 }  // namespace jgb

@@ -197,6 +197,42 @@ def test_persistent_replays_continue(oracle_mod, dtype):
     assert np.array_equal(got, J.interior_of(oracle_mod.jacobi(u0, 33)))
 
 
+@pytest.mark.parametrize("ws", ["1", "0"])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_persistent_kernels_vs_oracle(oracle_mod, monkeypatch, dtype, ws):
+    """Both persistent kernels (warp-specialised, JACOBI_PERSIST_WS=1, and
+    barrier-driven, 0) on uneven grids with ragged and 64-wide blocks, at
+    several work-item shapes: iterates bit-exact with the oracle, a fused
+    residual within 1e-12, and a solve that stops at the oracle's check."""
+    monkeypatch.setenv("JACOBI_PERSIST_WS", ws)
+    grids = [(70, 64, 37), (45, 37, 29), (33, 18, 50)]
+    splits = [("shape", (64, 64, 64)), ("count", (3, 5, 2)), ("shape", (11, 9, 16))]
+    inits = [dict(bc="uniform", bc_seed=61 + g, interior="uniform", interior_seed=71 + g) for g in range(3)]
+    npdt = np.float64 if dtype == "f64" else np.float32
+    u0 = [J.initial_grid(*grids[g], dtype=npdt, **inits[g]) for g in range(3)]
+    want = [oracle_mod.jacobi(u0[g], 9) for g in range(3)]
+    for zc, cw in ((0, 8), (1, 8), (2, 2)):
+        with jg.Jacobi3D(grids, splits, dtype, inits, path="persistent") as s:
+            if zc:
+                s.set_shape(zc, cw)
+            s.step(4)
+            s.step(5)
+            s.sync()
+            rel, ab = s.residual()
+            for g in range(3):
+                assert np.array_equal(s.copy_out(g), J.interior_of(want[g])), (zc, cw, g)
+                rn, _, orel = oracle_mod.residual(want[g])
+                assert abs(ab[g] - rn) <= RES_TOL * rn and abs(rel[g] - orel) <= RES_TOL * orel
+    zi = [dict(bc="uniform", bc_seed=61 + g, interior="zero") for g in range(3)]
+    with jg.Jacobi3D(grids, splits, dtype, zi, path="persistent") as s:
+        its, rels, sts = s.solve(1e-5, 5000, 10)
+        got = [s.copy_out(g) for g in range(3)]
+    for g in range(3):
+        ou, k, orel, ost = oracle_mod.solve(J.initial_grid(*grids[g], dtype=npdt, **zi[g]), 1e-5, 5000, 10)
+        assert (its[g], sts[g]) == (k, ost), g
+        assert np.array_equal(got[g], J.interior_of(ou)), g
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_residual_parity(oracle_mod, dtype):
     grid = (37, 29, 41)
@@ -342,14 +378,19 @@ def _cfg2():
 
 def test_config2_full_size_vs_oracle(oracle_mod):
     """Full 512^3 grid, the benchmark's launch configuration, 260 iterations (the
-    front from the boundary has reached every point), compared bit for bit."""
+    front from the boundary has reached every point), compared bit for bit;
+    the residual norms (|b - Au|, |b| and rel, over blocks whose planes are
+    split into two row windows) within 1e-12 of the oracle's."""
     w, init = _cfg2()
     u0 = J.initial_grid(*w["grid"], **init)
     want = oracle_mod.jacobi(u0, 260)
     with _solver(w["grid"], w["split"], "f64", init, "graph") as s:
         s.step(260)
         got = s.copy_out()
+        rel, ab = s.residual()
     assert np.array_equal(got, J.interior_of(want))
+    rn, bn, orel = oracle_mod.residual(want)
+    assert abs(ab[0] - rn) <= RES_TOL * rn and abs(rel[0] - orel) <= RES_TOL * orel
 
 
 def test_weak_scaling_slab_full_size_vs_oracle(oracle_mod):

@@ -10,9 +10,15 @@ workload is the 512^3 FP64 grid in 8x8x8 blocks of 64^3, 1000 iterations per
 step; its two state copies (2.1 GB) exceed L2, so no flush is needed between
 steps.
 
-Output: ONE JSON line on rank 0 (see the keys below).  `--impl reference`
-times the CPU oracle instead (the slow, obviously-correct program the CUDA
-path is checked against), on a bounded sample of the same workload.
+Output: ONE JSON line on rank 0.  Beside the headline keys it carries
+`configs`, one entry per workload of the benchmark set, each with its own
+config name and its own fixed step count (they do not scale with --steps):
+the 64^3 latency case, the 512^3 exchange forms and halo share, the 256-grid
+FP32 and FP64 batches, the 768^3 FP32 grid (HBM roofline, error against
+FP64), the 1536x768x512 slab, the FP32 precision study and the serving
+stream; `--no-extras` leaves them out.  `--impl reference` times the CPU
+oracle instead (the slow, obviously-correct program the CUDA path is checked
+against), on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -53,12 +59,14 @@ def parse_args():
                    help="oracle iterations in the CPU sample (about 7 s on 16 Arm cores at 512^3)")
     p.add_argument("--no-sweep", action="store_true", help="skip the channel ping-pong sweep")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    p.add_argument("--serve-requests", type=int, default=200,
+    p.add_argument("--serve-requests", type=int, default=10000,
                    help="requests of the serving workload to run (0 = skip; 10000 = the full workload)")
-    p.add_argument("--precision", action="store_true",
-                   help="also run the FP32-state precision study (768^3 and 96^3/192^3 proxies)")
+    p.add_argument("--no-precision", action="store_true",
+                   help="skip the FP32-state precision study (768^3 and 96^3/192^3 proxies)")
     p.add_argument("--serve-baseline", type=int, default=100,
-                   help="requests re-solved by the plain per-grid FP64 launch loop")
+                   help="first requests served alone and re-solved by the plain per-grid FP64 launch loop")
+    p.add_argument("--no-extras", action="store_true",
+                   help="headline workload only (no per-config entries, sweeps, serving or precision study)")
     return p.parse_args()
 
 
@@ -93,6 +101,32 @@ def ncu_traffic(workload: str):
     if d.get("source_sha") != kernel_source_sha():
         return None, d
     return d.get("dram_bytes_per_launch"), d
+
+
+def ncu_record(workload: str):
+    """The committed ncu summary of the workload's step kernel when it was taken
+    from the current kernel sources, else None."""
+    traffic, rec = ncu_traffic(workload)
+    return rec if (rec is not None and traffic is not None) else None
+
+
+def instruction_roof(rec, n_points, sm_mhz, n_sm):
+    """Hardware-derived ceilings of one step launch from its committed ncu
+    counters: each pipe's executed warp instructions per launch against that
+    pipe's peak issue rate (warp instructions per SM per cycle, as ncu reports
+    it) x SMs x the SM clock sampled during the timed region; `issue` is all
+    instructions against the schedulers' issue rate.  Returns GLUP/s ceilings
+    per pipe, or None without counters."""
+    if not rec or "inst_per_launch" not in rec or not sm_mhz:
+        return None
+    inst, peak = rec["inst_per_launch"], rec["peak_inst_per_sm_cycle"]
+    out = {}
+    for pipe, n in inst.items():
+        if n and peak.get(pipe):
+            t = n / (peak[pipe] * n_sm * sm_mhz * 1e6)
+            out[pipe] = {"warp_inst_per_launch": n, "thread_inst_per_lup": 32 * n / n_points,
+                         "peak_warp_inst_per_sm_cycle": peak[pipe], "bound_GLUPs": n_points / t / 1e9}
+    return out or None
 
 
 class ClockSampler:
@@ -192,12 +226,15 @@ def workload_config(name, grids, splits, dtype, iters, path):
     return cfg
 
 
-def cpu_baseline(name, iters_sample, single_thread=False):
+def cpu_baseline(name, iters_sample, single_thread=False, warm_calls=0):
     """The oracle as it stands on the host cores, on a bounded sample: the first
     `iters_sample` iterations of the workload (for a batch, of its first grids
-    up to about 64 M points).  With `single_thread`, also one iteration of the
-    first sampled grid on one core (the oracle's result does not depend on the
-    thread count)."""
+    up to about 64 M points).  `warm_calls` one-iteration samples run first,
+    as the reference arm's warm-up steps do.  With `single_thread`, also one
+    iteration of the first sampled grid on one core (the oracle's result does
+    not depend on the thread count)."""
+    for _ in range(warm_calls):
+        cpu_baseline(name, 1)
     import jacobi_inputs as J
     import numpy as np
     import oracle
@@ -296,15 +333,10 @@ SERVE_CFG = dict(tol=1e-6, cap=20000, check_every=100, block=(32, 32, 32), budge
                  stall_checks=20, noise_amp=1e-3)
 
 
-def serving_bench(jg, J, n_requests, n_baseline):
-    """Continuous batching of Jacobi solves (FP32 state, FP64 residual):
-    Poisson arrivals (mean 2 ms), lognormal sides clipped to [32, 256], 32^3
-    blocks, stop at 1e-6 relative residual or 20,000 iterations.  Returns
-    latency percentiles, solves/s, the served LUP rate and the same requests
-    solved one by one by the plain per-grid FP64 launch loop."""
+def serve_stream(jg, reqs, inits):
+    """Serve `reqs` (Poisson arrivals replayed in real time by a submitter
+    thread) through one server; latency percentiles, solves/s, served LUP rate."""
     c = SERVE_CFG
-    reqs = J.serving_requests(n_requests)
-    inits = [dict(bc="linear_noise", bc_seed=r["seed"], noise_amp=c["noise_amp"], interior="zero") for r in reqs]
     split = ("shape", c["block"])
     s = jg.serve_create(c["budget"], c["slots"], "f32", check_every=c["check_every"], round_checks=1,
                         stall_checks=c["stall_checks"])
@@ -338,13 +370,28 @@ def serving_bench(jg, J, n_requests, n_baseline):
     statuses = {k: sum(1 for r in res if r.status == v) for k, v in
                 (("converged", 0), ("max_iters", 1), ("stagnated", 2))}
     q = lambda f: lat_ms[min(len(lat_ms) - 1, int(f * len(lat_ms)))]
-    out = {"requests": len(reqs), "solves_per_s": len(reqs) / span_s, "p50_ms": q(0.50), "p99_ms": q(0.99),
-           "offered_req_per_s": len(reqs) / max(reqs[-1]["arrival_s"], 1e-9), "wall_s": span_s,
-           "served_GLUPs": stats.lups / span_s / 1e9, "statuses": statuses, "rounds": stats.rounds,
-           "dtype": "f32 state, f64 residual", "config": dict(c, budget=int(c["budget"]))}
+    return {"requests": len(reqs), "solves_per_s": len(reqs) / span_s, "p50_ms": q(0.50), "p99_ms": q(0.99),
+            "offered_req_per_s": len(reqs) / max(reqs[-1]["arrival_s"], 1e-9), "wall_s": span_s,
+            "served_GLUPs": stats.lups / span_s / 1e9, "statuses": statuses, "rounds": stats.rounds}
+
+
+def serving_bench(jg, J, n_requests, n_baseline):
+    """Continuous batching of Jacobi solves (FP32 state, FP64 residual):
+    Poisson arrivals (mean 2 ms), lognormal sides clipped to [32, 256], 32^3
+    blocks, stop at 1e-6 relative residual or 20,000 iterations.  The whole
+    stream first; then its first `n_baseline` requests served alone (same
+    arrival times) and solved one by one by the plain per-grid FP64 launch
+    loop, so the two solves/s figures compared come from the same requests."""
+    c = SERVE_CFG
+    reqs = J.serving_requests(n_requests)
+    inits = [dict(bc="linear_noise", bc_seed=r["seed"], noise_amp=c["noise_amp"], interior="zero") for r in reqs]
+    out = serve_stream(jg, reqs, inits)
+    out.update(dtype="f32 state, f64 residual", config=dict(c, budget=int(c["budget"])))
     nb = min(n_baseline, len(reqs))
     if nb > 0:
         import torch
+        sub = serve_stream(jg, reqs[:nb], inits[:nb])
+        split = ("shape", c["block"])
         t1 = time.perf_counter()
         base_status = {"converged": 0, "max_iters": 0, "stagnated": 0}
         for i in range(nb):
@@ -353,16 +400,20 @@ def serving_bench(jg, J, n_requests, n_baseline):
                 base_status[("converged", "max_iters", "stagnated")[st[0]]] += 1
         torch.cuda.synchronize()
         bt = time.perf_counter() - t1
-        out["fp64_launch_loop"] = {"requests": nb, "solves_per_s": nb / bt, "wall_s": bt, "statuses": base_status,
-                                   "note": "one kernel launch per iteration, residual read on the host at each check"}
-        out["served_solves_per_s_vs_launch_loop"] = out["solves_per_s"] / (nb / bt)
+        out["same_requests"] = {
+            "requests": nb, "served": sub,
+            "fp64_launch_loop": {"solves_per_s": nb / bt, "wall_s": bt, "statuses": base_status,
+                                 "note": "one kernel launch per iteration, residual read on the host at each "
+                                         "check, requests one after another"},
+            "served_vs_launch_loop": sub["solves_per_s"] / (nb / bt)}
     return out
 
 
 def channel_modes(jg, torch, s, stream):
     """One-way latency of the three exchange forms the paper compares (Sec.
     4.2.1), all between the same two blocks of one GPU: the device channel
-    driven from the host (send + receive kernels, completion by stream sync),
+    driven from the host (the receive posted first, then one send launch that
+    delivers into it, completion by stream sync),
     the GPU Messaging form (the device copy is posted only after a host-side
     metadata message) and host staging (device->host, host hand-off,
     host->device).  The device-resident ping-pong above is the channel with no
@@ -383,8 +434,10 @@ def channel_modes(jg, torch, s, stream):
                     for _ in range(rounds if not warm else 5):
                         for a, b in ((0, 1), (1, 0)):
                             if mode == "channel":
-                                jg.channel_send(ch, a, src.data_ptr(), n, stream)
+                                # the receive is posted first, so the send delivers
+                                # straight into dst in one launch
                                 jg.channel_recv(ch, b, dst.data_ptr(), n, stream)
+                                jg.channel_send(ch, a, src.data_ptr(), n, stream)
                                 stream.synchronize()
                             elif mode == "messaging":
                                 jg.channel_send_msg(ch, a, src.data_ptr(), n, stream)
@@ -477,8 +530,134 @@ def precision_study(jg, J, np):
     return out
 
 
+def timed_steps(s, iters, steps, stream, torch):
+    """Milliseconds of each of `steps` calls of s.step(iters), by CUDA events
+    on the handle's stream."""
+    out = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(iters)
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def glups(points, iters, ms):
+    return points * iters / (ms * 1e-3) / 1e9
+
+
+def halo_share(jg, s, iters, stream, torch, reps=3):
+    """Halo share of a step: the step time minus the time of the same kernels
+    with every face store kept in the block (jacobi_measure_local_halo), over
+    the step time; normal and local runs alternate.  Leaves the exchange on;
+    the state is no longer a Jacobi iterate afterwards."""
+    t_norm, t_loc = [], []
+    for _ in range(reps):
+        jg.jacobi_measure_local_halo(s.h, 0)
+        t_norm += timed_steps(s, iters, 1, stream, torch)
+        jg.jacobi_measure_local_halo(s.h, 1)
+        t_loc += timed_steps(s, iters, 1, stream, torch)
+    jg.jacobi_measure_local_halo(s.h, 0)
+    tn, tl = statistics.median(t_norm), statistics.median(t_loc)
+    return {"share": (tn - tl) / tn, "ms_per_iter": tn / iters, "ms_per_iter_faces_local": tl / iters,
+            "iters": iters, "reps": reps,
+            "definition": "(step time - step time with every face stored into the block's own slots) / step time"}
+
+
+def exchange_forms(jg, J, torch, name, iters, stream):
+    """Per-iteration compute and halo-exchange time of every exchange form on
+    one workload (jacobi_step_timed): fused device channel (graph path, the
+    exchange inside the stencil), explicit device pack + copy, and the three
+    host-driven forms of the paper (channel with pre-posted slots, GPU
+    messaging, host staging)."""
+    grids, splits, inits, dtype, _ = J.workload_grids(name)
+    n_points = sum(g[0] * g[1] * g[2] for g in grids)
+    out = {"iters": iters}
+    with jg.Jacobi3D(grids, splits, dtype, inits, path="graph", stream=stream) as s:
+        payload = s.info.halo_bytes_per_iter
+        for path in ("graph", "explicit", "channel", "messaging", "host_staged"):
+            s.set_path(path)
+            s.step_timed(max(2, iters // 10))  # warm-up (graph capture, pinned buffers)
+            comp, exch = s.step_timed(iters)
+            tot = (comp + exch) / iters
+            out[path] = {"us_per_iter": 1e3 * tot, "compute_us_per_iter": 1e3 * comp / iters,
+                         "exchange_us_per_iter": 1e3 * exch / iters, "GLUPs": glups(n_points, 1, tot),
+                         "halo_GBps": payload / (tot * 1e-3) / 1e9 if tot > 0 else None,
+                         "exchange_share": exch / (comp + exch) if comp + exch > 0 else 0.0}
+    out["halo_payload_bytes_per_iter"] = payload
+    ex = {k: out[k]["exchange_us_per_iter"] for k in ("explicit", "channel", "messaging", "host_staged")}
+    it = {k: out[k]["us_per_iter"] for k in ("graph", "explicit", "channel", "messaging", "host_staged")}
+    out["speedups"] = {
+        "exchange_host_staged_over_channel": ex["host_staged"] / ex["channel"],
+        "exchange_host_staged_over_messaging": ex["host_staged"] / ex["messaging"],
+        "exchange_messaging_over_channel": ex["messaging"] / ex["channel"],
+        "iteration_host_staged_over_channel": it["host_staged"] / it["channel"],
+        "iteration_host_staged_over_fused": it["host_staged"] / it["graph"],
+        "note": "the paper's Jacobi3D D/H comparison (Sec. 4.3) is GPU-aware (channel, messaging) against host "
+                "staging; the fused device channel removes the host from the exchange altogether"}
+    return out
+
+
+def config_bench(jg, J, torch, name, stream, steps, iters=None, paths=("graph",), peaks=None, err_vs_f64=False,
+                 share=False):
+    """GLUP/s of one named workload on the given paths (`steps` timed steps of
+    `iters` iterations after one warm-up step), the per-launch roofline view
+    (FP32: HBM, 8 B per update; FP64: the same HBM view, the step being bound
+    by its arithmetic pipes), optionally the halo share and the FP32 result's
+    error against the FP64 path after the same iterations (relative inf-norm;
+    the FP64 path is bit-exact with the oracle)."""
+    grids, splits, inits, dtype, w_iters = J.workload_grids(name)
+    iters = iters or w_iters
+    n_points = sum(g[0] * g[1] * g[2] for g in grids)
+    elem = 8 if dtype == "f64" else 4
+    out = {"workload": name, "dtype": dtype, "iters_per_step": iters, "steps": steps, "n_grids": len(grids),
+           "points": n_points}
+    for path in paths:
+        with jg.Jacobi3D(grids, splits, dtype, inits, path="graph" if path == "auto" else path, stream=stream) as s:
+            tuned = s.autotune(min(iters, 50)) if path == "auto" else None
+            timed_steps(s, iters, 1, stream, torch)
+            ms = timed_steps(s, iters, steps, stream, torch)
+            best = min(ms)
+            info = s.info
+            row = {"GLUPs": glups(n_points, iters * steps, sum(ms)), "GLUPs_best_step": glups(n_points, iters, best),
+                   "us_per_iter": 1e3 * sum(ms) / (steps * iters), "kind_items": s.kind_items(),
+                   "shape": {"zchunk": info.zchunk, "cw_cap": info.cw_cap}}
+            if tuned:
+                row["autotune"] = tuned
+            hbm = 2 * elem * n_points / (sum(ms) * 1e-3 / (steps * iters)) / 1e9
+            if peaks:
+                row["roofline_hbm"] = {"achieved_GBps": hbm, "peak": peaks["hbm_gbs"], "frac": hbm / peaks["hbm_gbs"],
+                                       "bytes_per_update": 2 * elem}
+            if share and path == paths[0]:
+                row["halo"] = dict(halo_share(jg, s, iters, stream, torch), payload_bytes_per_iter=
+                                   s.info.halo_bytes_per_iter)
+            out[path] = row
+    if err_vs_f64 and dtype == "f32":
+        import numpy as np
+        res = {}
+        for dt in ("f32", "f64"):
+            with jg.Jacobi3D(grids, splits, dt, inits, path="graph", stream=stream) as s:
+                s.step(w_iters)
+                res[dt] = [s.copy_out(g) for g in range(len(grids))]
+        err = 0.0
+        for a, b in zip(res["f32"], res["f64"]):
+            err = max(err, float(np.max(np.abs(a.astype(np.float64) - b)) / np.max(np.abs(b))))
+        out["err_vs_fp64"] = {"iterations": w_iters, "rel_inf": err, "bar": 1e-5}
+    return out
+
+
 def run_ours(args):
     world, rank, local = dist_setup(args)
+    # The CPU oracle's sample first, before any GPU work, with the reference
+    # arm's warm-up (so both arms time the same program the same way).
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cb = cpu_baseline(args.workload, args.cpu_iters, single_thread=True, warm_calls=args.warmup)
+        cb.pop("seconds", None)
+        cb.pop("lups", None)
+
     import torch
     import jacobi_inputs as J
     import paper_2102_12416_gb300 as jg
@@ -501,6 +680,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     n_points = sum(g[0] * g[1] * g[2] for g in grids)
     elem = 8 if dtype == "f64" else 4
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
 
     # ---- device-resident timing ------------------------------------------------
     s = jg.Jacobi3D(grids, splits, dtype, inits, path="graph" if args.path == "auto" else args.path, stream=stream)
@@ -544,8 +724,12 @@ def run_ours(args):
     launch_s = stencil_ms * 1e-3 / (args.steps * iters)
     peaks, peak_kind = measured_peaks()
     traffic, _ = ncu_traffic(args.workload)
+    rec = ncu_record(args.workload)
     kname = ("k_stream<%s> / k_tiles<%s> (fused stencil + face pack)" % (("double",) * 2 if dtype == "f64"
                                                                           else ("float",) * 2))
+    hbm_view = {"algorithmic_GBps": 2 * elem * n_points / launch_s / 1e9, "peak": peaks["hbm_gbs"],
+                "frac": 2 * elem * n_points / launch_s / 1e9 / peaks["hbm_gbs"], "peak_kind": peak_kind,
+                "bytes_per_update": 2 * elem}
     if dtype == "f64":
         # An FP64 update is 5 adds + 1 multiply.  Inside the integer adder's
         # domain the kernel may run adds on the integer pipe as well as the
@@ -565,12 +749,17 @@ def run_ours(args):
                     "fp64_pipe_only_view": {"achieved_GFLOPs": 6 * achieved, "peak": FP64_ADDMUL_PEAK_GFLOPS,
                                             "frac": 6 * achieved / FP64_ADDMUL_PEAK_GFLOPS,
                                             "peak_kind": "nominal FP64 1.25 TFLOP/s (FMA=2) -> 0.625 T add/mul per s"},
-                    "hbm_view": {"algorithmic_GBps": 2 * elem * n_points / launch_s / 1e9,
-                                 "peak": peaks["hbm_gbs"],
-                                 "frac": 2 * elem * n_points / launch_s / 1e9 / peaks["hbm_gbs"],
-                                 "peak_kind": peak_kind}}
+                    "hbm_view": hbm_view}
+        roof = instruction_roof(rec, n_points, clk.get("sm_mhz"), n_sm)
+        if roof:
+            lim = min(v["bound_GLUPs"] for v in roof.values())
+            roofline["instruction_view"] = {
+                "pipes": roof, "bound_GLUPs": lim, "frac": achieved / lim,
+                "peak_kind": "per pipe: executed warp instructions per launch (committed ncu counters) over the "
+                             "pipe's peak issue rate x %d SMs x the median SM clock sampled in the timed region "
+                             "(%s MHz)" % (n_sm, clk.get("sm_mhz"))}
     else:
-        achieved = 2 * elem * n_points / launch_s / 1e9
+        achieved = hbm_view["algorithmic_GBps"]
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname,
                     "peak_kind": peak_kind}
@@ -611,27 +800,46 @@ def run_ours(args):
            "steps": e2e_steps, "phase_ms_per_step": {k: round(v, 3) for k, v in phases.items()}}
 
     sweep = modes = bw = None
-    if not args.no_sweep and rank == 0:
+    extras = rank == 0 and not args.no_extras
+    if extras and not args.no_sweep:
         sweep = channel_sweep(jg, torch, s, stream)
         modes = channel_modes(jg, torch, s, stream)
         bw = channel_bw(jg, torch, s, stream)
     s.close()
     del h_in, h_out
 
+    configs = None
+    if extras:
+        configs = {}
+        c1 = config_bench(jg, J, torch, "jacobi3d-fp64-64c-2x2x2", stream, 5,
+                          paths=("graph", "persistent", "fused", "auto"))
+        c1["exchange_forms"] = exchange_forms(jg, J, torch, "jacobi3d-fp64-64c-2x2x2", 100, stream)
+        configs["jacobi3d-fp64-64c-2x2x2"] = c1
+        configs["jacobi3d-fp64-512c-8x8x8"] = {
+            "headline": "see value / roofline above",
+            "halo": None, "exchange_forms": exchange_forms(jg, J, torch, "jacobi3d-fp64-512c-8x8x8", 20, stream)}
+        with jg.Jacobi3D(grids, splits, dtype, inits, path="graph", stream=stream) as s2:
+            timed_steps(s2, 100, 1, stream, torch)
+            configs["jacobi3d-fp64-512c-8x8x8"]["halo"] = dict(
+                halo_share(jg, s2, 100, stream, torch), payload_bytes_per_iter=s2.info.halo_bytes_per_iter)
+        for name in ("jacobi3d-batched256-fp32", "jacobi3d-batched256-fp64"):
+            configs[name] = config_bench(jg, J, torch, name, stream, 3, paths=("graph", "persistent", "auto"),
+                                         peaks=peaks)
+        c4 = config_bench(jg, J, torch, "jacobi3d-fp32-768c-12x12x12", stream, 5, peaks=peaks, err_vs_f64=True,
+                          share=True)
+        c4["graph"]["roofline_hbm"]["traffic"] = ncu_traffic("jacobi3d-fp32-768c-12x12x12")[0]
+        configs["jacobi3d-fp32-768c-12x12x12"] = c4
+        configs["jacobi3d-fp64-1536x768x512"] = config_bench(jg, J, torch, "jacobi3d-fp64-1536x768x512", stream, 3,
+                                                              peaks=peaks)
+
     precision = None
-    if rank == 0 and args.precision:
+    if extras and not args.no_precision:
         import numpy as np
         precision = precision_study(jg, J, np)
 
     serving = None
-    if rank == 0 and args.serve_requests > 0:
+    if extras and args.serve_requests > 0:
         serving = serving_bench(jg, J, args.serve_requests, args.serve_baseline)
-
-    cb = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        cb = cpu_baseline(args.workload, args.cpu_iters, single_thread=True)
-        cb.pop("seconds", None)
-        cb.pop("lups", None)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
@@ -641,8 +849,8 @@ def run_ours(args):
                                parallelism=f"replicas{world}" if world > 1 else "single-gpu", autotune=tuned),
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "halo": halo, "final_rel_residual": rel[0] if rel else None,
-                "channel_pingpong": sweep, "channel_modes": modes, "channel_bandwidth": bw,
-                "serving": serving, "precision": precision}
+                "configs": configs, "precision": precision, "serving": serving,
+                "channel_pingpong": sweep, "channel_modes": modes, "channel_bandwidth": bw}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -73,3 +73,18 @@ def test_reference_arm_line_single_rank():
     assert line["e2e"] == {"value": line["value"], "unit": "GLUP/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert line["cpu_baseline"]["value"] == line["value"] and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_instruction_roof_from_counters():
+    """Per-pipe ceilings: executed warp instructions per launch over the pipe's
+    peak issue rate x SMs x clock; the tightest pipe bounds the kernel."""
+    import bench
+    rec = {"inst_per_launch": {"alu": 4.0e8, "fp64": 1.25e7, "issue": 6.4e8},
+           "peak_inst_per_sm_cycle": {"alu": 2.0, "fp64": 0.0625, "issue": 4.0}}
+    roof = bench.instruction_roof(rec, 1 << 27, 2000.0, 100)
+    t_alu = 4.0e8 / (2.0 * 100 * 2000e6)
+    assert abs(roof["alu"]["bound_GLUPs"] - (1 << 27) / t_alu / 1e9) < 1e-9
+    assert abs(roof["alu"]["thread_inst_per_lup"] - 32 * 4.0e8 / (1 << 27)) < 1e-9
+    assert min(roof, key=lambda k: roof[k]["bound_GLUPs"]) == "fp64"
+    assert bench.instruction_roof(None, 1, 2000.0, 100) is None
+    assert bench.instruction_roof(rec, 1, None, 100) is None

@@ -79,7 +79,7 @@ def test_instruction_roof_from_counters():
     """Per-pipe ceilings: executed warp instructions per launch over the pipe's
     peak issue rate x SMs x clock; the tightest pipe bounds the kernel."""
     import bench
-    rec = {"inst_per_launch": {"alu": 4.0e8, "fp64": 1.25e7, "issue": 6.4e8},
+    rec = {"inst_per_launch": {"alu": 4.0e8, "fp64": 1.5e7, "issue": 6.4e8},
            "peak_inst_per_sm_cycle": {"alu": 2.0, "fp64": 0.0625, "issue": 4.0}}
     roof = bench.instruction_roof(rec, 1 << 27, 2000.0, 100)
     t_alu = 4.0e8 / (2.0 * 100 * 2000e6)

@@ -230,7 +230,7 @@ __global__ void k_emu_reset(GridNorm* norms, const int32_t* grid_ids, int n) {
 // Self-test of the integer-pipe adder: out[i] = dadd_nn(a[i], b[i]).
 __global__ void k_selftest_dadd(const double* a, const double* b, int64_t n, double* out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t j = i < n ? i : n - 1;  // every lane takes part in the adder's vote
+  const int64_t j = i < n ? i : n - 1;  // clamped index: every lane loads in bounds
   const double r = dadd_nn(a[j], b[j]);
   if (i < n) out[i] = r;
 }

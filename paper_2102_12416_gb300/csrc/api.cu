@@ -626,9 +626,10 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
   const int smem = 128 + h->stages * (int32_t)h->plan.max_stage;
   const int threads = persistent_threads(h->active_items.data(), h->active_items.size());
   // The warp-specialised kernel takes launches whose items are all streamed
-  // (no tiles), whose units have at most 8 partners and whose CTAs own at most
-  // kPersistCache units each; the barrier-driven kernel takes the others.
-  int ws_cw = 0, maxc = 0;
+  // (no tiles), whose units have at most 8 partners and whose CTAs' unit
+  // tables fit in shared memory beside the ring; the barrier-driven kernel
+  // takes the others.
+  int ws_cw = 0, maxc = 0, ws_smem = 0, cache_units = 0;
   if (h->persist_ws) {
     bool tiles = false;
     int cw = 2;
@@ -640,11 +641,26 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
     for (size_t u = 0; u + 1 < h->active_dep_off.size(); ++u)
       maxdep = std::max(maxdep, h->active_dep_off[u + 1] - h->active_dep_off[u]);
     if (!tiles && maxdep <= 8 && !h->active_units.empty()) {
-      const int m = persistent_max_ctas(h->plan.dtype, smem, 0, cw);
+      // The tables of every unit a CTA owns follow the ring; more tables mean
+      // fewer resident CTAs and so more units per CTA: grow the table count
+      // until it covers the units per CTA of the launch it allows.
       const int64_t nu = (int64_t)h->active_units.size();
-      if (m > 0 && (nu + std::min<int64_t>(m, nu) - 1) / std::min<int64_t>(m, nu) <= kPersistCache) {
-        ws_cw = cw;
-        maxc = m;
+      const int ub = persist_ws_unit_bytes();
+      int64_t cu = 1;
+      for (int rep = 0; rep < 16; ++rep) {
+        const int64_t sm = smem + cu * ub;
+        if (sm > kPersistWsSmem) break;
+        const int m = persistent_max_ctas(h->plan.dtype, (int)sm, 0, cw);
+        if (m <= 0) break;
+        const int64_t per = (nu + std::min<int64_t>(m, nu) - 1) / std::min<int64_t>(m, nu);
+        if (per <= cu) {
+          ws_cw = cw;
+          maxc = m;
+          ws_smem = (int)sm;
+          cache_units = (int)cu;
+          break;
+        }
+        cu = per;
       }
     }
   }
@@ -673,19 +689,21 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
   a.resid_first = resid_first ? 1 : 0;
   a.dtype = h->plan.dtype;
   a.stages = h->stages;
-  a.smem = smem;
+  a.smem = ws_cw ? ws_smem : smem;
   a.norms = h->d_norms;
   a.emu = h->fp64_emu;
   a.threads = threads;
   a.ws_cw = ws_cw;
   a.stage_bytes = (int32_t)h->plan.max_stage;
+  a.cache_units = cache_units;
   const int ctas = std::min(maxc, a.n_units);
   // Replay a captured graph of the same launch shape; the start iteration
   // goes to device memory first (a pageable source is staged before the call
   // returns, so the stack variable may go).
   jacobi_s::PersistGraph& pg = h->pgraph[resid_first ? 1 : 0];
   if (!h->pgraph_off && (!pg.exec || pg.n_iters != n || pg.n_units != a.n_units || pg.stages != a.stages ||
-                         pg.ctas != ctas || pg.threads != threads || pg.ws_cw != ws_cw)) {
+                         pg.ctas != ctas || pg.threads != threads || pg.ws_cw != ws_cw ||
+                         pg.smem != a.smem || pg.cache_units != a.cache_units)) {
     if (pg.exec) cudaGraphExecDestroy(pg.exec);
     pg.exec = nullptr;
     PersistLaunch c = a;
@@ -729,6 +747,8 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
       pg.ctas = ctas;
       pg.threads = threads;
       pg.ws_cw = ws_cw;
+      pg.smem = a.smem;
+      pg.cache_units = a.cache_units;
     }
   }
   if (!h->pgraph_off && pg.exec) {

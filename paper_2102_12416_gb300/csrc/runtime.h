@@ -160,7 +160,7 @@ struct jacobi_s {
   struct PersistGraph {
     cudaGraphExec_t exec = nullptr;
     int64_t n_iters = 0;
-    int32_t n_units = -1, stages = 0, ctas = 0, threads = 0, ws_cw = 0;
+    int32_t n_units = -1, stages = 0, ctas = 0, threads = 0, ws_cw = 0, smem = 0, cache_units = 0;
   } pgraph[2];
   bool persist_ws = true;         // warp-specialised persistent kernel where it applies
   bool pgraph_off = false;        // capture of the cooperative launch failed: launch directly

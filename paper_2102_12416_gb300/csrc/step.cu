@@ -720,6 +720,7 @@ struct UnitCache {
 };
 static_assert(kPersistCache * sizeof(UnitCache) + 512 <= 227 * 1024 - kMaxStepSmem,
               "the persistent kernel's static shared memory must fit beside the largest ring");
+static_assert(sizeof(UnitCache) % 8 == 0, "unit tables follow the ring at 8-byte alignment");
 
 // NT threads per CTA (64, 128 or 256): the host picks the smallest that
 // covers every streamed row window of the launch (a window of W rows and V
@@ -847,6 +848,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_persist(PersistLaunc
 // ---------------------------------------------------------------------------
 // RESID: the launch runs one iteration and fuses the residual of its state
 // (separate instantiations keep the plain sweep's register allocation).
+// Every unit of the CTA has its tables cached in dynamic shared memory after
+// the ring (a.cache_units entries, which the host sizes to the units per CTA).
 // Registers are capped at 96 per thread.
 template <typename T, int CW, bool RESID>
 __global__ void __launch_bounds__(StreamShape<CW>::threads, 65536 / (StreamShape<CW>::threads * 96))
@@ -856,14 +859,14 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, 65536 / (StreamShape
   uint64_t* full = (uint64_t*)smem;
   uint64_t* empty = full + 8;
   unsigned char* stages = smem + 128;
-  __shared__ UnitCache s_u[kPersistCache];
+  UnitCache* s_u = (UnitCache*)(stages + (size_t)a.stages * (size_t)a.stage_bytes);
   __shared__ uint64_t s_done;
   __shared__ double s_red[2][CW];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = (int)gridDim.x, S = a.stages;
   const size_t SB = (size_t)a.stage_bytes;
   const int mine = a.n_units > (int)blockIdx.x ? (a.n_units - (int)blockIdx.x + G - 1) / G : 0;
-  if (mine > kPersistCache) {  // the host never launches this (CTA-uniform, before any barrier)
+  if (mine > a.cache_units) {  // the host never launches this (CTA-uniform, before any barrier)
     if (tid == 0) atomicCAS(a.err, (uint32_t)DEV_OK, (uint32_t)DEV_SEQ);
     return;
   }
@@ -899,7 +902,10 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, 65536 / (StreamShape
   __syncthreads();
   if (warp == CW) {
     // ---- producer ----
+    // ring position of the next plane: stage pst, filled pfill times before
     int64_t g = 0;
+    int pst = 0;
+    uint32_t pfill = 0;
     bool ok = true;
     for (int64_t t = 0; t < a.n_iters && ok; ++t) {
       const int64_t it = it0 + t;
@@ -920,13 +926,15 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, 65536 / (StreamShape
             const StageLayout L = stage_layout<T>(U.B, w.ya, w.yb);
             const int nplanes = w.z1 - w.z0 + 2;
             for (int j = 0; j < nplanes; ++j, ++g) {
-              const int st = (int)(g % S);
-              const int64_t fill = g / S;
-              if (fill > 0 && !mbar_ready(empty + st, (uint32_t)(fill - 1) & 1u, a.err, a.wait_ns)) {
+              if (pfill > 0 && !mbar_ready(empty + pst, (pfill - 1u) & 1u, a.err, a.wait_ns)) {
                 ok = false;
                 break;
               }
-              issue_plane<T>(U.B, p, w.z0, nplanes, j, w.ya, w.yb, L, stages + (size_t)st * SB, full + st);
+              issue_plane<T>(U.B, p, w.z0, nplanes, j, w.ya, w.yb, L, stages + (size_t)pst * SB, full + pst);
+              if (++pst == S) {
+                pst = 0;
+                ++pfill;
+              }
             }
           }
         }
@@ -944,7 +952,22 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, 65536 / (StreamShape
     return;
   }
   // ---- consumers ----
-  int64_t g = 0, nitem = 0;
+  // Ring positions (stage, fill parity) are advanced incrementally: c0 is the
+  // next item's first plane.  (Stage and parity from a plane counter would
+  // cost a 64-bit division by the run-time depth per use.)
+  struct Pos {
+    int st;
+    uint32_t ph;
+  };
+  const auto adv = [S](Pos x) {
+    if (++x.st == S) {
+      x.st = 0;
+      x.ph ^= 1u;
+    }
+    return x;
+  };
+  Pos c0{0, 0u};
+  uint32_t nitem = 0;
   for (int64_t t = 0; t < a.n_iters; ++t) {
     const int64_t it = it0 + t;
     constexpr bool resid = RESID;
@@ -962,21 +985,20 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, 65536 / (StreamShape
         const bool rag = item_ragged(w);
         const int tx = tid % txv, j0 = w.ya + (tid / txv) * 4;
         const bool active = j0 < w.yb;
-        auto stage_of = [&](int64_t x) { return stages + (size_t)(x % S) * SB; };
-        auto ready = [&](int64_t x) {
-          return mbar_ready(full + (x % S), (uint32_t)(x / S) & 1u, a.err, a.wait_ns);
-        };
+        auto ready = [&](Pos x) { return mbar_ready(full + x.st, x.ph, a.err, a.wait_ns); };
+        // planes qq - 1, qq, qq + 1 of the item
+        Pos pm = c0, pc = adv(c0), pp = adv(pc);
         double acc = 0.0;
         bool good = true;
         for (int qq = 1; qq <= nplanes - 2 && good; ++qq) {
-          if (qq == 1) good = ready(g) && ready(g + 1);
-          good = good && ready(g + qq + 1);
+          if (qq == 1) good = ready(pm) && ready(pc);
+          good = good && ready(pp);
           good = __all_sync(0xffffffffu, good) != 0;
           if (!good) break;
           if (active) {
-            const unsigned char* sm = stage_of(g + qq - 1);
-            const unsigned char* sc = stage_of(g + qq);
-            const unsigned char* sp = stage_of(g + qq + 1);
+            const unsigned char* sm = stages + (size_t)pm.st * SB;
+            const unsigned char* sc = stages + (size_t)pc.st * SB;
+            const unsigned char* sp = stages + (size_t)pp.st * SB;
             const int kq = w.z0 - 1 + qq;
             constexpr int MODE = RESID ? (kWrite | kPack | kResid) : (kWrite | kPack);
             if (rag) {
@@ -988,15 +1010,18 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, 65536 / (StreamShape
             }
           }
           __syncwarp();
-          if (lane == 0) mbar_arrive(empty + ((g + qq - 1) % S));
+          if (lane == 0) mbar_arrive(empty + pm.st);
+          pm = pc;
+          pc = pp;
+          pp = adv(pp);
         }
         if (!good) return;  // the error word is set; the producer drains its copies
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive(empty + ((g + nplanes - 2) % S));
-          mbar_arrive(empty + ((g + nplanes - 1) % S));
+          mbar_arrive(empty + pm.st);
+          mbar_arrive(empty + pc.st);
         }
-        g += nplanes;
+        c0 = pp;
         // item end: every consumer warp has stored its part
         if (resid) {
           for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -1108,7 +1133,7 @@ template <typename T, int CW, bool R>
 const void* persist_ws_fn_t() {
   static bool attr_set = false;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(k_persist_ws<T, CW, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxStepSmem) !=
+    if (cudaFuncSetAttribute(k_persist_ws<T, CW, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistWsSmem) !=
         cudaSuccess)
       return nullptr;
     attr_set = true;
@@ -1179,6 +1204,8 @@ int persistent_max_ctas(int dtype, int smem, int threads, int ws_cw) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem) != cudaSuccess) return 0;
   return per_sm * sms;
 }
+
+int persist_ws_unit_bytes() { return (int)sizeof(UnitCache); }
 
 cudaError_t launch_persistent(const PersistLaunch& a, int grid_ctas, cudaStream_t s) {
   if (a.n_units <= 0 || a.n_iters <= 0) return cudaSuccess;

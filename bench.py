@@ -775,6 +775,11 @@ def run_ours(args):
     e2e_steps = max(args.e2e_steps, 1)
     # phase boundaries on the same stream (set_state | step | residual | copy_out)
     pev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(e2e_steps)]
+    # one untimed round trip first: the first host transfer of a handle sizes
+    # its staging buffer (a one-time allocation, not part of a step)
+    for gi in range(len(grids)):
+        jg.jacobi_set_state(s.h, gi, h_in[gi].data_ptr(), False, stream)
+        jg.jacobi_copy_out(s.h, gi, h_out[gi].data_ptr(), False, jg.JACOBI_LAYOUT_INTERIOR, stream)
     torch.cuda.synchronize()
     e0.record(stream)
     for k in range(e2e_steps):

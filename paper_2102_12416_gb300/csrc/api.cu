@@ -341,6 +341,7 @@ int plan_build(int64_t n_grids, const jacobi_dim3* grids, const jacobi_split* sp
   P->off_pdep_ids = take(8 * nu * sizeof(int32_t));
   P->off_active_blocks = take(nb * sizeof(int32_t));
   P->off_it0 = take(sizeof(int64_t));
+  P->off_ticket = take(sizeof(unsigned long long));
   const size_t per16 = 32;  // plane pitch rounded to 32 elements
   for (auto& B : P->blocks) {
     B.pitch = (int64_t)align_up((size_t)(B.rx * B.ry), per16);
@@ -626,10 +627,9 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
   const int smem = 128 + h->stages * (int32_t)h->plan.max_stage;
   const int threads = persistent_threads(h->active_items.data(), h->active_items.size());
   // The warp-specialised kernel takes launches whose items are all streamed
-  // (no tiles), whose units have at most 8 partners and whose CTAs' unit
-  // tables fit in shared memory beside the ring; the barrier-driven kernel
-  // takes the others.
-  int ws_cw = 0, maxc = 0, ws_smem = 0, cache_units = 0;
+  // (no tiles) and whose units have at most 8 partners; the barrier-driven
+  // kernel takes the others.
+  int ws_cw = 0, maxc = 0;
   if (h->persist_ws) {
     bool tiles = false;
     int cw = 2;
@@ -640,27 +640,11 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
     int maxdep = 0;
     for (size_t u = 0; u + 1 < h->active_dep_off.size(); ++u)
       maxdep = std::max(maxdep, h->active_dep_off[u + 1] - h->active_dep_off[u]);
-    if (!tiles && maxdep <= 8 && !h->active_units.empty()) {
-      // The tables of every unit a CTA owns follow the ring; more tables mean
-      // fewer resident CTAs and so more units per CTA: grow the table count
-      // until it covers the units per CTA of the launch it allows.
-      const int64_t nu = (int64_t)h->active_units.size();
-      const int ub = persist_ws_unit_bytes();
-      int64_t cu = 1;
-      for (int rep = 0; rep < 16; ++rep) {
-        const int64_t sm = smem + cu * ub;
-        if (sm > kPersistWsSmem) break;
-        const int m = persistent_max_ctas(h->plan.dtype, (int)sm, 0, cw);
-        if (m <= 0) break;
-        const int64_t per = (nu + std::min<int64_t>(m, nu) - 1) / std::min<int64_t>(m, nu);
-        if (per <= cu) {
-          ws_cw = cw;
-          maxc = m;
-          ws_smem = (int)sm;
-          cache_units = (int)cu;
-          break;
-        }
-        cu = per;
+    if (!tiles && maxdep <= 8 && !h->active_units.empty() && smem <= kPersistWsSmem) {
+      const int m = persistent_max_ctas(h->plan.dtype, smem, 0, cw);
+      if (m > 0) {
+        ws_cw = cw;
+        maxc = m;
       }
     }
   }
@@ -689,21 +673,20 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
   a.resid_first = resid_first ? 1 : 0;
   a.dtype = h->plan.dtype;
   a.stages = h->stages;
-  a.smem = ws_cw ? ws_smem : smem;
+  a.smem = smem;
   a.norms = h->d_norms;
   a.emu = h->fp64_emu;
   a.threads = threads;
   a.ws_cw = ws_cw;
   a.stage_bytes = (int32_t)h->plan.max_stage;
-  a.cache_units = cache_units;
+  a.ticket = h->d_ticket;
   const int ctas = std::min(maxc, a.n_units);
   // Replay a captured graph of the same launch shape; the start iteration
   // goes to device memory first (a pageable source is staged before the call
   // returns, so the stack variable may go).
   jacobi_s::PersistGraph& pg = h->pgraph[resid_first ? 1 : 0];
   if (!h->pgraph_off && (!pg.exec || pg.n_iters != n || pg.n_units != a.n_units || pg.stages != a.stages ||
-                         pg.ctas != ctas || pg.threads != threads || pg.ws_cw != ws_cw ||
-                         pg.smem != a.smem || pg.cache_units != a.cache_units)) {
+                         pg.ctas != ctas || pg.threads != threads || pg.ws_cw != ws_cw)) {
     if (pg.exec) cudaGraphExecDestroy(pg.exec);
     pg.exec = nullptr;
     PersistLaunch c = a;
@@ -747,10 +730,10 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
       pg.ctas = ctas;
       pg.threads = threads;
       pg.ws_cw = ws_cw;
-      pg.smem = a.smem;
-      pg.cache_units = a.cache_units;
     }
   }
+  // the warp-specialised kernel hands out its work from a counter that starts at zero
+  if (ws_cw) JGB_CUDA(cudaMemsetAsync(h->d_ticket, 0, sizeof(unsigned long long), s));
   if (!h->pgraph_off && pg.exec) {
     const int64_t v = it0;
     JGB_CUDA(cudaMemcpyAsync(h->d_it0, &v, sizeof v, cudaMemcpyHostToDevice, s));
@@ -1150,6 +1133,7 @@ int jacobi_create_batch(int64_t n_grids, const jacobi_dim3* grids, const jacobi_
   h->d_pdep_ids = (int32_t*)(h->ws + P.off_pdep_ids);
   h->d_active_blocks = (int32_t*)(h->ws + P.off_active_blocks);
   h->d_it0 = (int64_t*)(h->ws + P.off_it0);
+  h->d_ticket = (unsigned long long*)(h->ws + P.off_ticket);
   if (const char* w = getenv("JACOBI_WAIT_MS")) {
     const double ms = atof(w);
     if (ms > 0) h->wait_ns = (uint64_t)(ms * 1e6);

@@ -31,10 +31,9 @@ constexpr int kMaxStepSmem = 227 * 1024 - 16384;
 // Units per CTA whose tables the barrier-driven persistent kernel caches in
 // static shared memory.
 constexpr int kPersistCache = 32;
-// Largest dynamic shared memory of the warp-specialised persistent kernel
-// (ring plus the tables of every unit of the CTA; its static shared memory is
-// a few hundred bytes).
-constexpr int kPersistWsSmem = 227 * 1024 - 1024;
+// Largest dynamic shared memory (the ring) of the warp-specialised persistent
+// kernel, beside its static queue of unit tables (about 2 KB).
+constexpr int kPersistWsSmem = 227 * 1024 - 4096;
 
 // A plane-streaming item encodes its consumer warps (2, 4 or 8) in the low
 // bits of y0 and, in bit 4, whether its block has padding (ragged rows or
@@ -167,13 +166,11 @@ struct PersistLaunch {
   int32_t threads;             // barrier-driven kernel: CTA size 64, 128 or 256 (persistent_threads)
   int32_t ws_cw;               // > 0: the warp-specialised kernel with this many consumer warps
   int32_t stage_bytes;         // ring stage stride of the warp-specialised kernel (largest stage)
-  int32_t cache_units;         // warp-specialised kernel: unit tables held after the ring (>= units per CTA)
+  unsigned long long* ticket;  // warp-specialised kernel: work counter, zero at launch
 };
 cudaError_t launch_persistent(const PersistLaunch& a, int grid_ctas, cudaStream_t s);
 // Co-resident CTA limit of the persistent kernel for (threads, ws_cw) (0 on error).
 int persistent_max_ctas(int dtype, int smem, int threads, int ws_cw = 0);
-// Shared-memory bytes of one unit's tables in the warp-specialised kernel.
-int persist_ws_unit_bytes();
 // Smallest persistent CTA (64, 128, 256 threads) that covers every item:
 // 32 * CW threads for streamed items of CW consumer warps, 256 for tiles.
 inline int persistent_threads(const WorkItem* items, size_t n) {

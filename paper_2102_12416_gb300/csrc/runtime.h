@@ -69,7 +69,7 @@ struct Plan {
   // byte offsets into the workspace
   size_t off_blocks, off_geom, off_items, off_active, off_kind, off_grids, off_norms, off_inits, off_gids, off_partials,
       off_progress, off_err, off_stage_tab, off_punit_items, off_punit_ids, off_pdep_off, off_pdep_ids,
-      off_active_blocks, off_it0;
+      off_active_blocks, off_it0, off_ticket;
   size_t off_stage_begin = 0, off_stage_end = 0;  // the explicit-path staging buffers, contiguous
   int64_t halo_faces = 0;                         // internal faces (one message each per iteration)
   size_t bytes = 0;
@@ -131,6 +131,7 @@ struct jacobi_s {
   int32_t* d_pdep_ids = nullptr;
   int32_t* d_active_blocks = nullptr;  // blocks of the active grids (exchange kernels)
   int64_t* d_it0 = nullptr;            // start iteration of a replayed persistent graph
+  unsigned long long* d_ticket = nullptr;  // work counter of the warp-specialised persistent kernel
 
   // host mirrors
   std::vector<jgb::WorkItem> active_items;
@@ -160,7 +161,7 @@ struct jacobi_s {
   struct PersistGraph {
     cudaGraphExec_t exec = nullptr;
     int64_t n_iters = 0;
-    int32_t n_units = -1, stages = 0, ctas = 0, threads = 0, ws_cw = 0, smem = 0, cache_units = 0;
+    int32_t n_units = -1, stages = 0, ctas = 0, threads = 0, ws_cw = 0;
   } pgraph[2];
   bool persist_ws = true;         // warp-specialised persistent kernel where it applies
   bool pgraph_off = false;        // capture of the cooperative launch failed: launch directly

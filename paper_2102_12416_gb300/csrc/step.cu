@@ -720,7 +720,6 @@ struct UnitCache {
 };
 static_assert(kPersistCache * sizeof(UnitCache) + 512 <= 227 * 1024 - kMaxStepSmem,
               "the persistent kernel's static shared memory must fit beside the largest ring");
-static_assert(sizeof(UnitCache) % 8 == 0, "unit tables follow the ring at 8-byte alignment");
 
 // NT threads per CTA (64, 128 or 256): the host picks the smallest that
 // covers every streamed row window of the launch (a window of W rows and V
@@ -829,28 +828,39 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_persist(PersistLaunc
 }
 
 // ---------------------------------------------------------------------------
-// Warp-specialised persistent kernel (all items plane-streamed, every unit of
-// the CTA cached): CW consumer warps and one producer warp per CTA, as in
-// k_stream, but the ring of S stages (stride: the largest stage) runs on
-// across items, units and iterations.  The producer warp, for each unit in
-// turn, acquire-waits (bounded, one lane per flag) until the unit's partners
-// and the unit itself have finished the previous iteration, then its lane 0
-// streams the unit's planes into the ring, reusing a stage once every
-// consumer warp has released it; so it prefetches the next unit, or the next
-// iteration's first unit, while the consumers compute.  The consumers compute
-// each plane as k_stream does, release stages, and at the end of every item
-// meet on an mbarrier (bounded wait; no named barrier, which a warp leaving on
-// an error could hang): then one thread writes the item's residual partial
-// and, after a unit's last item, release-stores progress[u] = it + 1.  Every
-// thread fences its generic stores against the async proxy before that
-// meeting, since other CTAs' bulk copies read them.  Planes carry a global
-// sequence number g (stage g % S, phase (g / S) & 1) shared by both roles.
+// Warp-specialised persistent kernel (all items plane-streamed): CW consumer
+// warps and one producer warp per CTA, as in k_stream, but the ring of S
+// stages (stride: the largest stage) runs on across items, units and
+// iterations, and CTAs take their work dynamically.  The launch's work is
+// n_iters x n_units tickets, handed out in order by one device counter
+// (ticket t = iteration t / n_units, active unit t % n_units).  The producer
+// warp takes a ticket, copies the unit's tables into a slot of a small
+// shared-memory queue, acquire-waits (bounded, one lane per flag) until the
+// unit's partners and the unit itself have finished the previous iteration,
+// publishes the slot to the consumers and streams the unit's planes into the
+// ring, reusing a stage once every consumer warp has released it; so it
+// prefetches the next unit while the consumers compute.  The consumers take
+// the queue's slots in order, compute each plane as k_stream does, release
+// stages, and at the end of every item meet on an mbarrier (bounded wait; no
+// named barrier, which a warp leaving on an error could hang): then one thread
+// writes the item's residual partial and, after a unit's last item,
+// release-stores progress[u] = it + 1.  Every thread fences its generic stores
+// against the async proxy before that meeting, since other CTAs' bulk copies
+// read them.
+// Progress: a ticket waits only on tickets of the previous iteration, which
+// are smaller.  The smallest unfinished ticket therefore has its partners
+// finished, its producer can issue its planes (the ring stages and queue
+// slots it needs are released by earlier, finished tickets of its CTA or by
+// its own consumers), so it finishes; all CTAs are co-resident (cooperative
+// launch).  Dynamic tickets let fast CTAs take more units, where a fixed
+// assignment left per-CTA busy times 20 % apart (placement, not work).
 // ---------------------------------------------------------------------------
 // RESID: the launch runs one iteration and fuses the residual of its state
 // (separate instantiations keep the plain sweep's register allocation).
-// Every unit of the CTA has its tables cached in dynamic shared memory after
-// the ring (a.cache_units entries, which the host sizes to the units per CTA).
-// Registers are capped at 96 per thread.
+// The host zeroes *a.ticket before every launch.  Registers are capped at 96
+// per thread.
+constexpr int kPersistQueue = 4;  // unit slots between the producer and the consumers
+
 template <typename T, int CW, bool RESID>
 __global__ void __launch_bounds__(StreamShape<CW>::threads, 65536 / (StreamShape<CW>::threads * 96))
     k_persist_ws(PersistLaunch a) {
@@ -859,86 +869,117 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, 65536 / (StreamShape
   uint64_t* full = (uint64_t*)smem;
   uint64_t* empty = full + 8;
   unsigned char* stages = smem + 128;
-  UnitCache* s_u = (UnitCache*)(stages + (size_t)a.stages * (size_t)a.stage_bytes);
+  __shared__ UnitCache s_q[kPersistQueue];
+  __shared__ int64_t s_qit[kPersistQueue];  // iteration of the slot's ticket; -1: no more work
+  __shared__ uint64_t s_qfull[kPersistQueue], s_qempty[kPersistQueue];
   __shared__ uint64_t s_done;
   __shared__ double s_red[2][CW];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int G = (int)gridDim.x, S = a.stages;
+  const int S = a.stages;
   const size_t SB = (size_t)a.stage_bytes;
-  const int mine = a.n_units > (int)blockIdx.x ? (a.n_units - (int)blockIdx.x + G - 1) / G : 0;
-  if (mine > a.cache_units) {  // the host never launches this (CTA-uniform, before any barrier)
-    if (tid == 0) atomicCAS(a.err, (uint32_t)DEV_OK, (uint32_t)DEV_SEQ);
-    return;
-  }
-  for (int k = warp; k < mine; k += CW + 1) {  // one warp per unit
-    const int ui = (int)blockIdx.x + k * G;
-    UnitCache& U = s_u[k];
-    const int q0 = a.unit_items[ui];
-    const BlockDev* Bg = a.blocks + a.items[q0].block;
-    const uint32_t* src = (const uint32_t*)Bg;
-    uint32_t* dst = (uint32_t*)&U.B;
-    for (int i = lane; i < (int)(sizeof(BlockDev) / 4); i += 32) dst[i] = src[i];
-    if (lane < 12) U.send[lane / 6][lane % 6] = Bg->send[lane % 6][lane / 6];
-    const int d0 = a.dep_off[ui], d1 = a.dep_off[ui + 1];
-    if (lane < kPersistDeps) U.dep[lane] = d0 + lane < d1 ? a.dep_ids[d0 + lane] : 0;
-    if (lane == 0) {
-      U.unit = a.unit_ids[ui];
-      U.q0 = q0;
-      U.q1 = a.unit_items[ui + 1];
-      U.ndep = d1 - d0;
-      U.start_iter = a.grids[Bg->grid].start_iter;
-      U.emu = (sizeof(T) == 8 && a.emu && a.norms && a.norms[Bg->grid].emu_bad == 0u) ? 1 : 0;
-    }
-  }
   if (tid == 0) {
     for (int st = 0; st < S; ++st) {
       mbar_init(full + st, 1);
       mbar_init(empty + st, CW);
+    }
+    for (int k = 0; k < kPersistQueue; ++k) {
+      mbar_init(s_qfull + k, 1);
+      mbar_init(s_qempty + k, CW);
     }
     mbar_init(&s_done, CW);
     mbar_fence_init();
   }
   const int64_t it0 = a.it0_dev ? *a.it0_dev : a.it0;
   __syncthreads();
+  const int64_t n_units = a.n_units;
+  const uint64_t total = (uint64_t)a.n_iters * (uint64_t)n_units;
   if (warp == CW) {
     // ---- producer ----
-    // ring position of the next plane: stage pst, filled pfill times before
-    int64_t g = 0;
-    int pst = 0;
-    uint32_t pfill = 0;
+    int64_t g = 0;       // planes issued (to drain after an error)
+    int pst = 0;         // ring stage of the next plane ...
+    uint32_t pfill = 0;  // ... and how often that stage was filled before
+    int qs = 0;          // queue slot of the next ticket ...
+    uint32_t qround = 0; // ... and how often the queue was passed through before
     bool ok = true;
-    for (int64_t t = 0; t < a.n_iters && ok; ++t) {
-      const int64_t it = it0 + t;
-      for (int k = 0; k < mine && ok; ++k) {
-        const UnitCache& U = s_u[k];
-        if (t > 0) {
-          bool okw = true;
-          if (lane < U.ndep) okw = wait_ge(a.progress + U.dep[lane], it, a.err, a.wait_ns);
-          else if (lane == U.ndep) okw = wait_ge(a.progress + U.unit, it, a.err, a.wait_ns);
-          ok = __all_sync(0xffffffffu, okw) != 0;
-          if (!ok) break;
-        }
+    for (;;) {
+      unsigned long long t = 0;
+      if (lane == 0) t = atomicAdd(a.ticket, 1ull);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      // the slot is free once every consumer warp finished its previous unit
+      if (qround > 0 && !mbar_ready(s_qempty + qs, (qround - 1u) & 1u, a.err, a.wait_ns)) {
+        ok = false;
+        break;
+      }
+      if (t >= total) {  // no work left: tell the consumers
         if (lane == 0) {
-          fence_proxy_async();
-          const int p = (int)((it - U.start_iter) & 1);
-          for (int q = U.q0; q < U.q1 && ok; ++q) {
-            const WorkItem w = a.items[q];
-            const StageLayout L = stage_layout<T>(U.B, w.ya, w.yb);
-            const int nplanes = w.z1 - w.z0 + 2;
-            for (int j = 0; j < nplanes; ++j, ++g) {
-              if (pfill > 0 && !mbar_ready(empty + pst, (pfill - 1u) & 1u, a.err, a.wait_ns)) {
-                ok = false;
-                break;
-              }
-              issue_plane<T>(U.B, p, w.z0, nplanes, j, w.ya, w.yb, L, stages + (size_t)pst * SB, full + pst);
-              if (++pst == S) {
-                pst = 0;
-                ++pfill;
-              }
+          s_qit[qs] = -1;
+          mbar_arrive(s_qfull + qs);
+        }
+        break;
+      }
+      const int64_t it = it0 + (int64_t)(t / (uint64_t)n_units);
+      const int ui = (int)(t % (uint64_t)n_units);
+      UnitCache& U = s_q[qs];
+      {
+        const int q0 = a.unit_items[ui];
+        const BlockDev* Bg = a.blocks + a.items[q0].block;
+        const uint32_t* src = (const uint32_t*)Bg;
+        uint32_t* dst = (uint32_t*)&U.B;
+        for (int i = lane; i < (int)(sizeof(BlockDev) / 4); i += 32) dst[i] = src[i];
+        if (lane < 12) U.send[lane / 6][lane % 6] = Bg->send[lane % 6][lane / 6];
+        const int d0 = a.dep_off[ui], d1 = a.dep_off[ui + 1];
+        if (lane < kPersistDeps) U.dep[lane] = d0 + lane < d1 ? a.dep_ids[d0 + lane] : 0;
+        if (lane == 0) {
+          U.unit = a.unit_ids[ui];
+          U.q0 = q0;
+          U.q1 = a.unit_items[ui + 1];
+          U.ndep = d1 - d0;
+          U.start_iter = a.grids[Bg->grid].start_iter;
+          U.emu = (sizeof(T) == 8 && a.emu && a.norms && a.norms[Bg->grid].emu_bad == 0u) ? 1 : 0;
+          s_qit[qs] = it;
+        }
+      }
+      __syncwarp();
+      if (it > it0) {  // the launch's first iteration follows earlier launches in stream order
+        bool okw = true;
+        const int nd = U.ndep;
+        if (lane < nd) okw = wait_ge(a.progress + U.dep[lane], it, a.err, a.wait_ns);
+        else if (lane == nd) okw = wait_ge(a.progress + U.unit, it, a.err, a.wait_ns);
+        ok = __all_sync(0xffffffffu, okw) != 0;
+        if (!ok) {  // the error word is set: let the consumers leave
+          if (lane == 0) {
+            s_qit[qs] = -1;
+            mbar_arrive(s_qfull + qs);
+          }
+          break;
+        }
+      }
+      if (lane == 0) {
+        fence_proxy_async();
+        mbar_arrive(s_qfull + qs);  // publish the slot (tables and iteration)
+        const int p = (int)((it - U.start_iter) & 1);
+        for (int q = U.q0; q < U.q1 && ok; ++q) {
+          const WorkItem w = a.items[q];
+          const StageLayout L = stage_layout<T>(U.B, w.ya, w.yb);
+          const int nplanes = w.z1 - w.z0 + 2;
+          for (int j = 0; j < nplanes; ++j, ++g) {
+            if (pfill > 0 && !mbar_ready(empty + pst, (pfill - 1u) & 1u, a.err, a.wait_ns)) {
+              ok = false;
+              break;
+            }
+            issue_plane<T>(U.B, p, w.z0, nplanes, j, w.ya, w.yb, L, stages + (size_t)pst * SB, full + pst);
+            if (++pst == S) {
+              pst = 0;
+              ++pfill;
             }
           }
         }
-        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      }
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) break;
+      if (++qs == kPersistQueue) {
+        qs = 0;
+        ++qround;
       }
     }
     if (!ok && lane == 0) {
@@ -968,78 +1009,87 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, 65536 / (StreamShape
   };
   Pos c0{0, 0u};
   uint32_t nitem = 0;
-  for (int64_t t = 0; t < a.n_iters; ++t) {
-    const int64_t it = it0 + t;
+  int qs = 0;
+  uint32_t qround = 0;
+  for (;;) {
+    if (!mbar_ready(s_qfull + qs, qround & 1u, a.err, a.wait_ns)) return;
+    const int64_t it = s_qit[qs];
+    if (it < 0) return;  // no work left (or the producer stopped on an error)
+    const UnitCache& U = s_q[qs];
     constexpr bool resid = RESID;
-    for (int k = 0; k < mine; ++k) {
-      const UnitCache& U = s_u[k];
-      const int p = (int)((it - U.start_iter) & 1);
-      PlaneView<T> O = plane_view<T>(U.B, p);
-      O.ss = U.send[p ^ 1];
-      const bool emu = U.emu != 0;
-      const int txv = O.rx / VEC;
-      for (int q = U.q0; q < U.q1; ++q, ++nitem) {
-        const WorkItem w = a.items[q];
-        const StageLayout L = stage_layout<T>(U.B, w.ya, w.yb);
-        const int nplanes = w.z1 - w.z0 + 2;
-        const bool rag = item_ragged(w);
-        const int tx = tid % txv, j0 = w.ya + (tid / txv) * 4;
-        const bool active = j0 < w.yb;
-        auto ready = [&](Pos x) { return mbar_ready(full + x.st, x.ph, a.err, a.wait_ns); };
-        // planes qq - 1, qq, qq + 1 of the item
-        Pos pm = c0, pc = adv(c0), pp = adv(pc);
-        double acc = 0.0;
-        bool good = true;
-        for (int qq = 1; qq <= nplanes - 2 && good; ++qq) {
-          if (qq == 1) good = ready(pm) && ready(pc);
-          good = good && ready(pp);
-          good = __all_sync(0xffffffffu, good) != 0;
-          if (!good) break;
-          if (active) {
-            const unsigned char* sm = stages + (size_t)pm.st * SB;
-            const unsigned char* sc = stages + (size_t)pc.st * SB;
-            const unsigned char* sp = stages + (size_t)pp.st * SB;
-            const int kq = w.z0 - 1 + qq;
-            constexpr int MODE = RESID ? (kWrite | kPack | kResid) : (kWrite | kPack);
-            if (rag) {
-              if (sizeof(T) == 8 && emu) acc += stream_plane<T, 4, MODE, true, true, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
-              else acc += stream_plane<T, 4, MODE, false, true, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
-            } else {
-              if (sizeof(T) == 8 && emu) acc += stream_plane<T, 4, MODE, true, false, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
-              else acc += stream_plane<T, 4, MODE, false, false, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
-            }
+    const int p = (int)((it - U.start_iter) & 1);
+    PlaneView<T> O = plane_view<T>(U.B, p);
+    O.ss = U.send[p ^ 1];
+    const bool emu = U.emu != 0;
+    const int txv = O.rx / VEC;
+    for (int q = U.q0; q < U.q1; ++q, ++nitem) {
+      const WorkItem w = a.items[q];
+      const StageLayout L = stage_layout<T>(U.B, w.ya, w.yb);
+      const int nplanes = w.z1 - w.z0 + 2;
+      const bool rag = item_ragged(w);
+      const int tx = tid % txv, j0 = w.ya + (tid / txv) * 4;
+      const bool active = j0 < w.yb;
+      auto ready = [&](Pos x) { return mbar_ready(full + x.st, x.ph, a.err, a.wait_ns); };
+      // planes qq - 1, qq, qq + 1 of the item
+      Pos pm = c0, pc = adv(c0), pp = adv(pc);
+      double acc = 0.0;
+      bool good = true;
+      for (int qq = 1; qq <= nplanes - 2 && good; ++qq) {
+        if (qq == 1) good = ready(pm) && ready(pc);
+        good = good && ready(pp);
+        good = __all_sync(0xffffffffu, good) != 0;
+        if (!good) break;
+        if (active) {
+          const unsigned char* sm = stages + (size_t)pm.st * SB;
+          const unsigned char* sc = stages + (size_t)pc.st * SB;
+          const unsigned char* sp = stages + (size_t)pp.st * SB;
+          const int kq = w.z0 - 1 + qq;
+          constexpr int MODE = RESID ? (kWrite | kPack | kResid) : (kWrite | kPack);
+          if (rag) {
+            if (sizeof(T) == 8 && emu) acc += stream_plane<T, 4, MODE, true, true, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+            else acc += stream_plane<T, 4, MODE, false, true, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+          } else {
+            if (sizeof(T) == 8 && emu) acc += stream_plane<T, 4, MODE, true, false, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+            else acc += stream_plane<T, 4, MODE, false, false, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
           }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(empty + pm.st);
-          pm = pc;
-          pc = pp;
-          pp = adv(pp);
         }
-        if (!good) return;  // the error word is set; the producer drains its copies
         __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(empty + pm.st);
-          mbar_arrive(empty + pc.st);
-        }
-        c0 = pp;
-        // item end: every consumer warp has stored its part
-        if (resid) {
-          for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-          if (lane == 0) s_red[nitem & 1][warp] = acc;
-        }
-        fence_proxy_async();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&s_done);
-        if (!mbar_ready(&s_done, (uint32_t)(nitem & 1), a.err, a.wait_ns)) return;
-        if (tid == 0) {
-          if (resid) {
-            double r = 0.0;
-            for (int c = 0; c < CW; ++c) r += s_red[nitem & 1][c];
-            a.partials[w.slot] = r;
-          }
-          if (q == U.q1 - 1) st_release(a.progress + U.unit, it + 1);
-        }
+        if (lane == 0) mbar_arrive(empty + pm.st);
+        pm = pc;
+        pc = pp;
+        pp = adv(pp);
       }
+      if (!good) return;  // the error word is set; the producer drains its copies
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(empty + pm.st);
+        mbar_arrive(empty + pc.st);
+      }
+      c0 = pp;
+      // item end: every consumer warp has stored its part
+      if (resid) {
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) s_red[nitem & 1][warp] = acc;
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&s_done);
+      if (!mbar_ready(&s_done, (uint32_t)(nitem & 1), a.err, a.wait_ns)) return;
+      if (tid == 0) {
+        if (resid) {
+          double r = 0.0;
+          for (int c = 0; c < CW; ++c) r += s_red[nitem & 1][c];
+          a.partials[w.slot] = r;
+        }
+        if (q == U.q1 - 1) st_release(a.progress + U.unit, it + 1);
+      }
+    }
+    // the slot may be refilled once every consumer warp is done with it
+    __syncwarp();
+    if (lane == 0) mbar_arrive(s_qempty + qs);
+    if (++qs == kPersistQueue) {
+      qs = 0;
+      ++qround;
     }
   }
 }
@@ -1204,8 +1254,6 @@ int persistent_max_ctas(int dtype, int smem, int threads, int ws_cw) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem) != cudaSuccess) return 0;
   return per_sm * sms;
 }
-
-int persist_ws_unit_bytes() { return (int)sizeof(UnitCache); }
 
 cudaError_t launch_persistent(const PersistLaunch& a, int grid_ctas, cudaStream_t s) {
   if (a.n_units <= 0 || a.n_iters <= 0) return cudaSuccess;

@@ -417,7 +417,9 @@ def channel_modes(jg, torch, s, stream):
     the GPU Messaging form (the device copy is posted only after a host-side
     metadata message) and host staging (device->host, host hand-off,
     host->device).  The device-resident ping-pong above is the channel with no
-    host in the loop at all."""
+    host in the loop at all.  Each form makes two library calls per message and
+    ends with the same stream synchronisation, so the harness costs the same
+    for all three."""
     nmax = 4 << 20
     ch = jg.channel_open(s.h, 2, 0, 1, nmax)
     src = torch.zeros(nmax, dtype=torch.uint8, device="cuda")
@@ -438,13 +440,15 @@ def channel_modes(jg, torch, s, stream):
                                 # straight into dst in one launch
                                 jg.channel_recv(ch, b, dst.data_ptr(), n, stream)
                                 jg.channel_send(ch, a, src.data_ptr(), n, stream)
-                                stream.synchronize()
                             elif mode == "messaging":
                                 jg.channel_send_msg(ch, a, src.data_ptr(), n, stream)
                                 jg.channel_recv_msg(ch, b, dst.data_ptr(), n, stream)
                             else:
                                 jg.channel_send_host(ch, a, src.data_ptr(), n, stream)
                                 jg.channel_recv_host(ch, b, dst.data_ptr(), n, stream)
+                            # the same completion step for every form (the Messaging and
+                            # host-staged receives have already waited inside the call)
+                            stream.synchronize()
                     dt = time.perf_counter() - t0
                 row[mode + "_us"] = round(dt * 1e6 / (2 * rounds), 2)
             jg.channel_sync(ch, stream)  # device-side errors of this size, once

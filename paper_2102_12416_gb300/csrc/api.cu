@@ -624,7 +624,8 @@ int step_graph(jacobi_t* h, int64_t it0, int64_t n, cudaStream_t s) {
 }
 
 int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaStream_t s) {
-  const int smem = 128 + h->stages * (int32_t)h->plan.max_stage;
+  int stages = h->stages;
+  int smem = 128 + stages * (int32_t)h->plan.max_stage;
   const int threads = persistent_threads(h->active_items.data(), h->active_items.size());
   // The warp-specialised kernel takes launches whose items are all streamed
   // (no tiles) and whose units have at most 8 partners; the barrier-driven
@@ -645,6 +646,16 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
       if (m > 0) {
         ws_cw = cw;
         maxc = m;
+      }
+      // Large stages (whole 64-wide planes) take one more stage of lookahead
+      // when it costs no resident CTA: same-box A/B, 768^3 FP32 620 -> 659
+      // GLUP/s, FP64 unchanged; small stages lose with it (256 FP32 grids of
+      // 32^3 blocks 539 -> 507), so they keep the default.
+      const int smem5 = smem + (int32_t)h->plan.max_stage;
+      if (m > 0 && !h->stages_fixed && stages == 4 && h->plan.max_stage >= 8192 && smem5 <= kPersistWsSmem &&
+          persistent_max_ctas(h->plan.dtype, smem5, 0, cw) == m) {
+        stages = 5;
+        smem = smem5;
       }
     }
   }
@@ -672,7 +683,7 @@ int step_persistent(jacobi_t* h, int64_t it0, int64_t n, bool resid_first, cudaS
   a.partials = h->d_partials;
   a.resid_first = resid_first ? 1 : 0;
   a.dtype = h->plan.dtype;
-  a.stages = h->stages;
+  a.stages = stages;
   a.smem = smem;
   a.norms = h->d_norms;
   a.emu = h->fp64_emu;
@@ -1146,7 +1157,10 @@ int jacobi_create_batch(int64_t n_grids, const jacobi_dim3* grids, const jacobi_
   if (const char* pw = getenv("JACOBI_PERSIST_WS")) h->persist_ws = atoi(pw) != 0;
   if (const char* st = getenv("JACOBI_STAGES")) {
     const int v = atoi(st);
-    if (v >= 3 && v <= 8) h->stages = v;
+    if (v >= 3 && v <= 8) {
+      h->stages = v;
+      h->stages_fixed = true;
+    }
   }
   if (128 + h->stages * (int64_t)P.max_stage > kMaxStepSmem) h->stages = 3;
   // Zero the workspace so the padding of every row, plane and slot starts
@@ -1337,6 +1351,7 @@ extern "C" int jacobi_autotune(jacobi_t* h, int64_t iters_per_trial, void* strea
       int rc2 = apply_shape(t, zc, cw, s);
       if (rc2) return rc2;
       t->stages = st;
+      t->stages_fixed = true;
       t->path = path;
       t->tables_dirty = true;
       double est = 0.0;
@@ -1387,6 +1402,7 @@ extern "C" int jacobi_autotune(jacobi_t* h, int64_t iters_per_trial, void* strea
   if (rc) return rc;
   h->path = r.path;
   h->stages = r.stages;
+  h->stages_fixed = true;
   h->tables_dirty = true;
   if (out) *out = r;
   return JACOBI_OK;

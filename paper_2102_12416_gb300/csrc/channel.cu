@@ -68,6 +68,10 @@ struct channel_s {
     size_t bytes;
   };
   std::deque<Posted> posted[2];   // per receiving endpoint, in message order
+  // the last message delivered straight into a posted receive at endpoint e,
+  // and the stream its send was issued on (-1: none yet)
+  int64_t direct_n[2] = {-1, -1};
+  void* direct_stream[2] = {nullptr, nullptr};
   void* hstage[2] = {nullptr, nullptr};  // pinned host staging of the host-staged form, per receiver
   std::deque<MsgMeta> mailbox[2];        // metadata messages waiting at endpoint e
   uint64_t msg_seq[2] = {0, 0};
@@ -117,10 +121,14 @@ __global__ void k_chan_send(ChanCtr* c, int to, uint32_t n, const void* src, voi
 // every earlier message to that endpoint has been consumed (so "consumed"
 // stays in order), copy, then publish the message as delivered and consumed
 // (it never occupies a slot).
+// With ordered set the host has shown that message n - 1 was itself delivered
+// straight into a posted receive by a send earlier on the same stream, which
+// published consumed = n before this launch: the poll is skipped.
 __global__ void k_chan_send_direct(ChanCtr* c, int to, uint32_t n, const void* src, void* dst, size_t bytes,
-                                   uint64_t wait_ns) {
+                                   uint64_t wait_ns, int ordered) {
   __shared__ int ok;
-  if (threadIdx.x == 0) ok = (n < 1) ? 1 : (wait_seq_ge(&c->consumed[to], n, &c->err, wait_ns) ? 1 : 0);
+  if (threadIdx.x == 0)
+    ok = (n < 1 || ordered) ? 1 : (wait_seq_ge(&c->consumed[to], n, &c->err, wait_ns) ? 1 : 0);
   __syncthreads();
   if (!ok) return;
   copy16(dst, src, bytes, (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
@@ -335,10 +343,13 @@ int channel_send(channel_t* ch, int64_t from_block, const void* src, size_t byte
     if (pr.bytes != bytes)
       return set_error(JACOBI_ESEQ, "channel %u: message %llu has %zu bytes, the posted receive expects %zu", ch->id,
                        (unsigned long long)pr.n, bytes, pr.bytes);
+    const int ordered = ch->direct_n[to] + 1 == (int64_t)ch->sent[from] && ch->direct_stream[to] == stream;
     k_chan_send_direct<<<copy_ctas(bytes), kChanThreads, 0, S(stream)>>>(ch->ctr, to, n, src, pr.dst, bytes,
-                                                                         ch->h->wait_ns);
+                                                                         ch->h->wait_ns, ordered);
     JGB_CUDA(cudaGetLastError());
     ch->posted[to].pop_front();
+    ch->direct_n[to] = (int64_t)ch->sent[from];
+    ch->direct_stream[to] = stream;
   } else {
     k_chan_send<<<copy_ctas(bytes), kChanThreads, 0, S(stream)>>>(ch->ctr, to, n, src, ch->slot[to][n & 1], bytes,
                                                                     ch->h->wait_ns);

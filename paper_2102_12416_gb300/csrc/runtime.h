@@ -167,7 +167,8 @@ struct jacobi_s {
   bool pgraph_off = false;        // capture of the cooperative launch failed: launch directly
 
   uint64_t wait_ns = 1000000000ull;
-  int32_t stages = 4;             // ring stages of the plane-streaming path
+  int32_t stages = 4;             // ring stages of the persistent kernel's plane streaming
+  bool stages_fixed = false;      // set by JACOBI_STAGES or the autotuner (else large stages may take 5)
   int32_t fp64_emu = 1;           // FP64 pair sums on the integer pipe when safe
   int64_t drop_block = -1;        // fault injection (persistent path)
   bool local_halo = false;        // halo-share measurement: face stores stay in the block

@@ -28,7 +28,8 @@
  *   JACOBI_WAIT_MS     limit of every device-side wait in milliseconds (default
  *                      1000); an expired wait ends the kernel with
  *                      JACOBI_ETIMEDOUT instead of spinning on;
- *   JACOBI_FP64_EMU=0  keeps every FP64 add on the FP64 pipe (see
+ *   JACOBI_FP64_EMU=0  keeps every FP64 add on the FP64 pipe, the FP64
+ *                      stencil's and the FP32 residual's (see
  *                      jacobi_selftest_dadd);
  *   JACOBI_STAGES      ring depth (3..8) of the persistent kernel;
  *   JACOBI_PERSIST_WS=0  keeps the persistent path on its barrier-driven
@@ -358,9 +359,10 @@ int jacobi_sync(jacobi_t* h, void* stream);
  * Dirichlet boundary).  Synchronises the stream. */
 int jacobi_read_face(jacobi_t* h, int64_t block, int32_t face, void* dst, void* stream);
 
-/* Test support for the FP64 stencil's integer-pipe adder: out[i] = a[i] + b[i]
- * (device arrays of n doubles) computed by the integer-pipe routine the FP64
- * step kernels use for the neighbour pair sums.  For a[i], b[i] >= 0 with
+/* Test support for the integer-pipe FP64 adder: out[i] = a[i] + b[i] (device
+ * arrays of n doubles) computed by the integer-pipe routine the FP64 step
+ * kernels use for the neighbour pair sums and the FP32 residual for the pair
+ * sums of its widened values.  For a[i], b[i] >= 0 with
  * exponent field < 2040 the result is the IEEE-754 round-to-nearest-even sum
  * bit for bit; other inputs give unspecified values (the step kernels never
  * pass them: a device check keeps such grids on the FP64 pipe).  Setting the

@@ -916,8 +916,7 @@ int compute_bnorm(jacobi_t* h, cudaStream_t s, int64_t grid) {
     g0 = (int32_t)grid;
     ng = 1;
   }
-  if (h->plan.dtype == JACOBI_F64)
-    JGB_CUDA(launch_emu_check(h->d_blocks + b0, nb, h->d_grids, h->d_norms, h->d_gids + g0, ng, h->iter, s));
+  JGB_CUDA(launch_emu_check(h->d_blocks + b0, nb, h->d_grids, h->d_norms, h->d_gids + g0, ng, h->iter, h->plan.dtype, s));
   JGB_CUDA(launch_bnorm(a, s));
   JGB_CUDA(launch_reduce(h->d_grids, h->d_norms, h->d_gids + g0, ng, h->d_partials, 1, s));
   return JACOBI_OK;

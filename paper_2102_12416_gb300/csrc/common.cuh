@@ -74,7 +74,7 @@ struct GridNorm {
   double r_norm2;       // |b - A u|^2 of the last residual evaluation
   double r_norm;        // sqrt(r_norm2)
   double rel;           // r_norm / |b| (r_norm when |b| == 0)
-  uint32_t emu_bad;     // FP64 state has a value outside dadd_nn's domain
+  uint32_t emu_bad;     // the state has a value outside dadd_nn's domain (widened, for FP32)
   uint32_t pad_;
 };
 

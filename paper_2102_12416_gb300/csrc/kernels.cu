@@ -202,22 +202,28 @@ __global__ void __launch_bounds__(kThreads) k_bnorm(StepLaunch a) {
   if (threadIdx.x == 0) a.partials[w.slot] = s;
 }
 
-// Flag every FP64 grid whose current state (interior at its parity and all six
+// Flag every grid whose current state (interior at its parity and all six
 // receive slots) holds a value outside the domain of the integer-pipe adder
-// dadd_nn; the step kernels then keep that grid on the FP64 pipe.  By the
+// dadd_nn; the step kernels then keep that grid's FP64 sums (the FP64
+// stencil's, and the FP32 residual's of widened values) on the FP64 pipe.  By the
 // discrete maximum principle Jacobi iterates stay within the range of the
 // boundary and initial data, so a state that passes keeps passing.
+template <typename T>
 __global__ void k_emu_check(const BlockDev* __restrict__ blocks, const GridDev* grids, GridNorm* norms, int64_t it) {
+  // FP64: the high word (sign clear, exponent below 2040); FP32: the whole
+  // word (sign clear, finite: widened, such a value is inside the domain)
+  constexpr int W = sizeof(T) / 4;
+  constexpr uint32_t kLimit = sizeof(T) == 8 ? kEmuHiLimit : 0x7F800000u;
   const BlockDev& B = blocks[blockIdx.x];
   const int p = (int)((it - grids[B.grid].start_iter) & 1);
   const uint32_t* U = (const uint32_t*)B.u[p];
   bool bad = false;
   const int64_t pitch = B.plane_pitch, rx = B.rx;
-  for_interior(B, [&](int i, int j, int k) { bad |= U[2 * (k * pitch + j * rx + i) + 1] >= kEmuHiLimit; });
+  for_interior(B, [&](int i, int j, int k) { bad |= U[W * (k * pitch + j * rx + i) + W - 1] >= kLimit; });
   for (int f = 0; f < 6; ++f) {
     const uint32_t* S = (const uint32_t*)B.recv[f][p];
     const int64_t m = face_elems(B, f);
-    for (int64_t e = threadIdx.x; e < m; e += blockDim.x) bad |= S[2 * e + 1] >= kEmuHiLimit;
+    for (int64_t e = threadIdx.x; e < m; e += blockDim.x) bad |= S[W * e + W - 1] >= kLimit;
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&norms[B.grid].emu_bad, 1u);
 }
@@ -392,9 +398,12 @@ cudaError_t launch_copy_faces(const BlockDev* blocks, const int32_t* ids, int32_
 }
 
 cudaError_t launch_emu_check(const BlockDev* blocks, int32_t n_blocks, const GridDev* grids, GridNorm* norms,
-                             const int32_t* grid_ids, int32_t n_grids, int64_t it, cudaStream_t s) {
+                             const int32_t* grid_ids, int32_t n_grids, int64_t it, int dtype, cudaStream_t s) {
   if (n_grids > 0) k_emu_reset<<<(n_grids + 127) / 128, 128, 0, s>>>(norms, grid_ids, n_grids);
-  if (n_blocks > 0) k_emu_check<<<n_blocks, 256, 0, s>>>(blocks, grids, norms, it);
+  if (n_blocks > 0) {
+    if (dtype == 0) k_emu_check<double><<<n_blocks, 256, 0, s>>>(blocks, grids, norms, it);
+    else k_emu_check<float><<<n_blocks, 256, 0, s>>>(blocks, grids, norms, it);
+  }
   return cudaGetLastError();
 }
 

@@ -113,7 +113,7 @@ cudaError_t launch_copy_desc(const CopyDesc* d, int32_t n, cudaStream_t s);
 // Domain check of the integer-pipe FP64 adder (sets GridNorm::emu_bad) and
 // its self-test.
 cudaError_t launch_emu_check(const BlockDev* blocks, int32_t n_blocks, const GridDev* grids, GridNorm* norms,
-                             const int32_t* grid_ids, int32_t n_grids, int64_t it, cudaStream_t s);
+                             const int32_t* grid_ids, int32_t n_grids, int64_t it, int dtype, cudaStream_t s);
 cudaError_t launch_selftest_dadd(const double* a, const double* b, int64_t n, double* out, cudaStream_t s);
 cudaError_t launch_selftest_widen(unsigned long long* bad, cudaStream_t s);
 cudaError_t launch_selftest_div6(unsigned long long* bad, cudaStream_t s);

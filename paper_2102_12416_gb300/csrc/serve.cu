@@ -231,9 +231,8 @@ int admit(serve_s* s, int si, const Req& q) {
   a.it = s->it;
   a.partials = s->d_partials;
   a.dtype = s->cfg.dtype;
-  if (s->cfg.dtype == JACOBI_F64)
-    ENG_CUDA(launch_emu_check(s->d_blocks + sl.block_base, (int32_t)nb, s->d_grids, s->d_norms, s->d_ids + si, 1,
-                              s->it, st));
+  ENG_CUDA(launch_emu_check(s->d_blocks + sl.block_base, (int32_t)nb, s->d_grids, s->d_norms, s->d_ids + si, 1,
+                            s->it, s->cfg.dtype, st));
   ENG_CUDA(launch_bnorm(a, st));
   ENG_CUDA(launch_reduce(s->d_grids, s->d_norms, s->d_ids + si, 1, s->d_partials, 1, st));
   // No synchronisation: a host-to-device cudaMemcpyAsync from pageable memory

@@ -103,12 +103,25 @@ template <> struct V16<double> {
 // only the additions and multiplications (same-box A/B: the 768^3 FP32
 // residual 10.5 -> 7.4 ms, the whole 200-iteration step with its residual
 // 684 -> 700 GLUP/s; residuals bit-identical).
-template <typename T>
+// r^2 for one point: r = s - 6u in FP64 (FP32 values widened exactly, the
+// neighbour sum recomputed in FP64 in the stencil's order).  With EMU (an
+// FP32 state inside the integer adder's domain: no sign bit, finite) the
+// three pair sums of the widened values run on the integer pipe (dadd_nn,
+// bit-identical to the FP64 pipe's addition there), which leaves the FP64
+// pipe five of its eight operations per point.  FP32 kernels use it only in
+// residual-only launches: same-box A/B, 768^3 residual 7.07 -> 5.87 ms,
+// while in the fused step-and-residual launches the extra code path spilled
+// (serving 84.0 -> 81.9 solves/s).
+template <typename T, bool EMU = false>
 __device__ __forceinline__ double resid2(T xm, T xp, T ym, T yp, T zm, T zp, T s, T c) {
   double s64, c64;
   if constexpr (sizeof(T) == 8) {
     s64 = (double)s;
     c64 = (double)c;
+  } else if constexpr (EMU) {
+    s64 = __dadd_rn(__dadd_rn(dadd_nn(widen_f32(xm), widen_f32(xp)), dadd_nn(widen_f32(ym), widen_f32(yp))),
+                    dadd_nn(widen_f32(zm), widen_f32(zp)));
+    c64 = widen_f32(c);
   } else {
     s64 = __dadd_rn(__dadd_rn(__dadd_rn(widen_f32(xm), widen_f32(xp)), __dadd_rn(widen_f32(ym), widen_f32(yp))),
                     __dadd_rn(widen_f32(zm), widen_f32(zp)));
@@ -316,6 +329,9 @@ __device__ __forceinline__ double stream_plane(const PlaneView<T>& O, int k, int
                                                const unsigned char* sm, const unsigned char* sc,
                                                const unsigned char* sp, int tx, int j0) {
   constexpr int VEC = V16<T>::N;
+  // EMU: the integer-pipe adder takes the FP64 stencil's pair sums and, in
+  // either precision, the residual's (FP32 sums themselves stay FP32 adds)
+  constexpr bool EMU_SUM = EMU && sizeof(T) == 8;
   const int nx = O.nx, ny = O.ny, nz = O.nz;
   const int rx = RAG ? O.rx : nx, ry = RAG ? O.ry : ny;  // equal without padding
   const int i0 = tx * VEC;
@@ -380,15 +396,15 @@ __device__ __forceinline__ double stream_plane(const PlaneView<T>& O, int k, int
       // FP64: the z pair of 2 of a thread's 8 points goes to the FP64 pipe,
       // shifting work off the busier integer pipe (same-box A/B +0.5 % on
       // 64^3 blocks, +1.9 % on 32^3; 3 or 4 of 8 gained less).
-      const T s = (q == VEC - 1 && r < 2) ? nsum_zn<T, EMU>(xm, xp, ym[q], yp[q], zm[q], zp[q])
-                                          : nsum<T, EMU>(xm, xp, ym[q], yp[q], zm[q], zp[q]);
+      const T s = (q == VEC - 1 && r < 2) ? nsum_zn<T, EMU_SUM>(xm, xp, ym[q], yp[q], zm[q], zp[q])
+                                          : nsum<T, EMU_SUM>(xm, xp, ym[q], yp[q], zm[q], zp[q]);
       // FP64 finishes each point at once (keeping the sum live to the end of
       // the loop made ptxas spill); FP32 finishes the vector after the loop
       // (one fallback branch per vector).
       if constexpr (sizeof(T) == 8) v[q] = finish1(s);
       else sv[q] = s;
       if (MODE & kResid) {
-        const double e2 = resid2<T>(xm, xp, ym[q], yp[q], zm[q], zp[q], s, c[r][q]);
+        const double e2 = resid2<T, EMU>(xm, xp, ym[q], yp[q], zm[q], zp[q], s, c[r][q]);
         acc += (!RAG || (q <= ql && j < ny)) ? e2 : 0.0;
       }
     }
@@ -463,6 +479,7 @@ __device__ double stream_item(const BlockDev& B, int p, const WorkItem& w, Ring&
   const StageLayout L = stage_layout<T>(B, w.ya, w.yb);
   PlaneView<T> O = plane_view<T>(B, p);
   O.ss = tab;
+  constexpr bool kEmuUse = sizeof(T) == 8 || MODE == kResid;  // FP32: residual-only launches
   const int nplanes = w.z1 - w.z0 + 2;
   auto issue = [&](int q) {
     const int st = q % S;
@@ -500,10 +517,10 @@ __device__ double stream_item(const BlockDev& B, int p, const WorkItem& w, Ring&
       const unsigned char* sp = ring.stages + (size_t)((q + 1) % S) * L.bytes;
       const int kq = w.z0 - 1 + q;
       if (rag) {
-        if (sizeof(T) == 8 && emu) acc += stream_plane<T, RY, MODE, true, true, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+        if (kEmuUse && emu) acc += stream_plane<T, RY, MODE, true, true, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
         else acc += stream_plane<T, RY, MODE, false, true, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
       } else {
-        if (sizeof(T) == 8 && emu) acc += stream_plane<T, RY, MODE, true, false, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
+        if (kEmuUse && emu) acc += stream_plane<T, RY, MODE, true, false, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
         else acc += stream_plane<T, RY, MODE, false, false, true>(O, kq, w.ya, L, sm, sc, sp, tx, j0);
       }
     }
@@ -643,7 +660,7 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, StreamShape<CW>::min
     }
   } else {
     // ---- consumers ----
-    const bool emu = sizeof(T) == 8 && a.emu && a.norms && a.norms[B.grid].emu_bad == 0u;
+    const bool emu = (sizeof(T) == 8 || MODE == kResid) && a.emu && a.norms && a.norms[B.grid].emu_bad == 0u;
     PlaneView<T> O = plane_view<T>(B, p);
     if (kSendTable) O.ss = s_send;
     const int txv = O.rx / VEC;
@@ -669,7 +686,7 @@ __global__ void __launch_bounds__(StreamShape<CW>::threads, StreamShape<CW>::min
         const unsigned char* sm = stages + (size_t)((q - 1) & Sm) * L.bytes;
         const unsigned char* sc = stages + (size_t)(q & Sm) * L.bytes;
         const unsigned char* sp = stages + (size_t)((q + 1) & Sm) * L.bytes;
-        if (sizeof(T) == 8 && emu)
+        if ((sizeof(T) == 8 || MODE == kResid) && emu)
           acc += stream_plane<T, RY, MODE, true, RAG, kSendTable, (CW < 8)>(O, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
         else
           acc += stream_plane<T, RY, MODE, false, RAG, kSendTable, (CW < 8)>(O, w.z0 - 1 + q, w.ya, L, sm, sc, sp, tx, j0);
@@ -755,7 +772,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_persist(PersistLaunc
         U.q1 = a.unit_items[ui + 1];
         U.ndep = d1 - d0;
         U.start_iter = a.grids[Bg->grid].start_iter;
-        U.emu = (sizeof(T) == 8 && a.emu && a.norms && a.norms[Bg->grid].emu_bad == 0u) ? 1 : 0;
+        U.emu = (a.emu && a.norms && a.norms[Bg->grid].emu_bad == 0u) ? 1 : 0;
       }
     }
   }
@@ -785,7 +802,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_persist(PersistLaunc
         Bp = &a.blocks[a.items[q0].block];
         ndep = a.dep_off[ui + 1] - a.dep_off[ui];
         start = a.grids[Bp->grid].start_iter;
-        emu = sizeof(T) == 8 && a.emu && a.norms && a.norms[Bp->grid].emu_bad == 0u;
+        emu = a.emu && a.norms && a.norms[Bp->grid].emu_bad == 0u;
       }
       if (t > 0 && tid < 32) {
         // One lane per partner: the flags are polled in parallel, so the wait

@@ -2,7 +2,9 @@
 round-to-nearest-even addition bit for bit on its domain (non-negative,
 exponent field < 2040); numpy's float64 addition is the reference.  And the
 step kernels give identical iterates whether the pair sums run on the integer
-pipe or on the FP64 pipe (JACOBI_FP64_EMU=0).  The FP32 residual's
+pipe or on the FP64 pipe (JACOBI_FP64_EMU=0), and the FP32 residual-only
+launches (pair sums of widened values on the integer pipe inside the domain)
+give identical norms either way.  The FP32 residual's
 integer-pipe widening (binary32 -> binary64) equals the conversion
 instruction on all 2^32 inputs, and so does the FP32 update's two-operation
 division by 6 against the division instruction sequence."""
@@ -89,6 +91,42 @@ def test_negative_values_keep_the_fp64_pipe(oracle_mod):
         s.step(40)
         got = s.copy_out()
     assert np.array_equal(got, J.interior_of(oracle_mod.jacobi(u, 40)))
+
+
+def test_fp32_residual_same_with_and_without_integer_adds(monkeypatch, oracle_mod):
+    """An FP32 state inside the adder's domain (non-negative, finite): the
+    residual-only launch's integer-pipe pair sums give the same |r|, |b| and
+    rel, bit for bit, as the FP64-pipe sums, and both match the oracle's FP64
+    residual of the FP32 state within the residual bar."""
+    grid, split = (45, 37, 29), ("shape", (16, 16, 16))
+    init = dict(bc="linear_noise", bc_seed=21, noise_amp=1e-3, interior="uniform", interior_seed=22)
+    u = J.initial_grid(*grid, dtype=np.float32, **init)
+    uk = oracle_mod.jacobi(u, 17)
+    rn, bn, rel = oracle_mod.residual(uk)
+    outs = []
+    for emu in ("1", "0"):
+        monkeypatch.setenv("JACOBI_FP64_EMU", emu)
+        with jg.Jacobi3D(grid, split, "f32", init, path="graph") as s:
+            s.step(17)
+            grel, gabs = s.residual()
+            outs.append((grel[0], gabs[0]))
+    assert outs[0] == outs[1]
+    assert abs(outs[0][1] - rn) <= 1e-12 * rn and abs(outs[0][0] - rel) <= 1e-12 * rel
+
+
+def test_fp32_negative_state_residual_keeps_the_fp64_pipe(oracle_mod):
+    """An FP32 state with negative values is outside the adder's domain: its
+    residual runs on the FP64 pipe and matches the oracle."""
+    nx, ny, nz = 33, 30, 28
+    u = J.initial_grid(nx, ny, nz, "uniform", bc_seed=23, interior="uniform", interior_seed=24,
+                       dtype=np.float32) - np.float32(0.5)
+    uk = oracle_mod.jacobi(u, 5)
+    rn, bn, rel = oracle_mod.residual(uk)
+    with jg.Jacobi3D((nx, ny, nz), ("shape", (16, 16, 16)), "f32") as s:
+        s.set_state(u)
+        s.step(5)
+        grel, gabs = s.residual()
+    assert abs(gabs[0] - rn) <= 1e-12 * rn and abs(grel[0] - rel) <= 1e-12 * rel
 
 
 def test_widen_f32_exhaustive():

@@ -31,7 +31,9 @@
  *   JACOBI_FP64_EMU=0  keeps every FP64 add on the FP64 pipe, the FP64
  *                      stencil's and the FP32 residual's (see
  *                      jacobi_selftest_dadd);
- *   JACOBI_STAGES      ring depth (3..8) of the persistent kernel;
+ *   JACOBI_STAGES      ring depth (3..8) of the persistent kernel (default
+ *                      4, or 5 for plane stages of 8 KB and more when the
+ *                      fifth stage costs no resident CTA);
  *   JACOBI_PERSIST_WS=0  keeps the persistent path on its barrier-driven
  *                      kernel (by default launches whose items are all
  *                      plane-streamed run the warp-specialised one);
@@ -189,8 +191,10 @@ typedef struct {
   int32_t path;
   int64_t halo_bytes_per_iter; /* face payload moved per iteration (bytes) */
   size_t workspace_bytes;
-  int32_t stages;        /* ring depth of the persistent kernel (the per-step
-                            streaming kernels use 4)                          */
+  int32_t stages;        /* ring depth of the persistent kernel as set (by
+                            JACOBI_STAGES or the autotuner; otherwise 4, which
+                            large stages may raise to 5 at launch); the
+                            per-step streaming kernels use 4                  */
   int32_t item_kinds;    /* kernel variants launched per iteration (fused paths) */
   int32_t fp64_int_adds; /* neighbour pair sums per update that may run on the
                             integer pipe (0 or 3) for grids inside the integer
@@ -269,8 +273,10 @@ int jacobi_info(const jacobi_t* h, jacobi_info_t* out);
 int jacobi_block(const jacobi_t* h, int64_t block, jacobi_block_info* out);
 
 /* Select the step path (jacobi_path).  The persistent launch uses at most as
- * many CTAs as can be co-resident on the GPU; each owns several units when
- * there are more. */
+ * many CTAs as can be co-resident on the GPU.  Its warp-specialised kernel
+ * hands out the launch's (iteration, unit) pairs in order from a device
+ * counter, so a CTA takes its next unit when it is free; the barrier-driven
+ * kernel gives CTA c the units c, c + G, c + 2G, ... */
 int jacobi_set_path(jacobi_t* h, int32_t path);
 
 /* Work-item shape of the step kernels (the library's addition; the block

@@ -623,8 +623,12 @@ def config_bench(jg, J, torch, name, stream, steps, iters=None, paths=("graph",)
     out = {"workload": name, "dtype": dtype, "iters_per_step": iters, "steps": steps, "n_grids": len(grids),
            "points": n_points}
     for path in paths:
-        with jg.Jacobi3D(grids, splits, dtype, inits, path="graph" if path == "auto" else path, stream=stream) as s:
-            tuned = s.autotune(min(iters, 50)) if path == "auto" else None
+        # "auto": the autotuner picks path, ring depth and shape; "persistent_tuned":
+        # one persistent launch per step with the shape and depth tuned for it
+        base = {"auto": "graph", "persistent_tuned": "persistent"}.get(path, path)
+        with jg.Jacobi3D(grids, splits, dtype, inits, path=base, stream=stream) as s:
+            tuned = (s.autotune(min(iters, 50)) if path == "auto" else
+                     s.autotune(min(iters, 50), path="persistent") if path == "persistent_tuned" else None)
             timed_steps(s, iters, 1, stream, torch)
             ms = timed_steps(s, iters, steps, stream, torch)
             best = min(ms)
@@ -836,8 +840,8 @@ def run_ours(args):
             configs["jacobi3d-fp64-512c-8x8x8"]["halo"] = dict(
                 halo_share(jg, s2, 100, stream, torch), payload_bytes_per_iter=s2.info.halo_bytes_per_iter)
         for name in ("jacobi3d-batched256-fp32", "jacobi3d-batched256-fp64"):
-            configs[name] = config_bench(jg, J, torch, name, stream, 3, paths=("graph", "persistent", "auto"),
-                                         peaks=peaks)
+            configs[name] = config_bench(jg, J, torch, name, stream, 3,
+                                         paths=("graph", "persistent", "persistent_tuned", "auto"), peaks=peaks)
         c4 = config_bench(jg, J, torch, "jacobi3d-fp32-768c-12x12x12", stream, 5, peaks=peaks, err_vs_f64=True,
                           share=True)
         c4["graph"]["roofline_hbm"]["traffic"] = ncu_traffic("jacobi3d-fp32-768c-12x12x12")[0]

@@ -306,6 +306,16 @@ int jacobi_set_shape(jacobi_t* h, int64_t zchunk, int32_t cw_cap, void* stream);
  * Synchronises the stream. */
 int jacobi_autotune(jacobi_t* h, int64_t iters_per_trial, void* stream, jacobi_tune_result* out);
 
+/* The same search restricted to one path (JACOBI_PATH_FUSED, _GRAPH or
+ * _PERSISTENT): every candidate shape on that path and, for PERSISTENT, the
+ * ring depths 3..6 at its best shape; applies the path and the fastest shape
+ * and depth to `h`.  For a caller that wants a given execution form (say, the
+ * whole run in one persistent launch) with the shape tuned for it.  Cached
+ * under a key of its own.  JACOBI_EINVAL for another path.  Synchronises the
+ * stream. */
+int jacobi_autotune_path(jacobi_t* h, int32_t path, int64_t iters_per_trial, void* stream,
+                         jacobi_tune_result* out);
+
 /* ---- state transfer ---------------------------------------------------------- */
 
 /* Replace the whole state of grid `grid` (boundary and interior) from a padded

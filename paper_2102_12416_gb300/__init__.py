@@ -129,6 +129,7 @@ _SIGS = {
     "jacobi_solve": (ctypes.c_int, [P, c_double, c_int64, c_int64, c_int64, P, P, P, P]),
     "jacobi_sync": (ctypes.c_int, [P, P]),
     "jacobi_autotune": (ctypes.c_int, [P, c_int64, P, ctypes.POINTER(jacobi_tune_result)]),
+    "jacobi_autotune_path": (ctypes.c_int, [P, c_int32, c_int64, P, ctypes.POINTER(jacobi_tune_result)]),
     "jacobi_set_shape": (ctypes.c_int, [P, c_int64, c_int32, P]),
     "jacobi_read_face": (ctypes.c_int, [P, c_int64, c_int32, P, P]),
     "jacobi_debug_drop_block": (ctypes.c_int, [P, c_int64]),
@@ -327,6 +328,15 @@ def jacobi_solve(h, n_grids, tol, max_iters, check_every, stall_checks=0, stream
 def jacobi_autotune(h, iters_per_trial, stream=None) -> jacobi_tune_result:
     out = jacobi_tune_result()
     _call("jacobi_autotune", h, iters_per_trial, _stream(stream), ctypes.byref(out))
+    return out
+
+
+def jacobi_autotune_path(h, path, iters_per_trial, stream=None) -> jacobi_tune_result:
+    """The autotuner's search restricted to one path ("fused", "graph" or
+    "persistent" or its jacobi_path value)."""
+    out = jacobi_tune_result()
+    _call("jacobi_autotune_path", h, PATHS[path] if isinstance(path, str) else int(path), iters_per_trial,
+          _stream(stream), ctypes.byref(out))
     return out
 
 
@@ -535,8 +545,11 @@ class Jacobi3D:
     def sync(self):
         jacobi_sync(self.h, self.stream)
 
-    def autotune(self, iters_per_trial=50) -> dict:
-        r = jacobi_autotune(self.h, iters_per_trial, self.stream)
+    def autotune(self, iters_per_trial=50, path=None) -> dict:
+        """Tune path, ring depth and work-item shape (path given: shape and
+        ring depth for that path only) and apply the result."""
+        r = (jacobi_autotune(self.h, iters_per_trial, self.stream) if path is None
+             else jacobi_autotune_path(self.h, path, iters_per_trial, self.stream))
         return {"path": PATH_NAMES[r.path], "stages": r.stages, "ms_per_iter": r.ms_per_iter,
                 "n_tried": r.n_tried, "from_cache": bool(r.from_cache), "zchunk": r.zchunk, "cw_cap": r.cw_cap}
 

@@ -1284,11 +1284,12 @@ extern "C" int jacobi_set_shape(jacobi_t* h, int64_t zchunk, int32_t cw_cap, voi
   return apply_shape(h, zchunk, cw_cap, S(stream));
 }
 
-extern "C" int jacobi_autotune(jacobi_t* h, int64_t iters_per_trial, void* stream, jacobi_tune_result* out) {
-  if (!h || iters_per_trial < 1) return set_error(JACOBI_EINVAL, "bad arguments to jacobi_autotune");
+// The search of jacobi_autotune; only_path >= 0 restricts it to that path
+// (jacobi_autotune_path), cached under its own key.
+static int autotune_search(jacobi_t* h, int64_t iters_per_trial, void* stream, jacobi_tune_result* out, int32_t only_path) {
   const cudaStream_t s = S(stream);
   const Plan& P = h->plan;
-  const uint64_t key = geometry_signature(P);
+  const uint64_t key = geometry_signature(P) ^ (only_path < 0 ? 0ull : 0x9E3779B97F4A7C15ull * (uint64_t)(only_path + 1));
   jacobi_tune_result r{};
   if (cache_lookup(key, &r)) {
     r.from_cache = 1;
@@ -1379,12 +1380,13 @@ extern "C" int jacobi_autotune(jacobi_t* h, int64_t iters_per_trial, void* strea
     // every shape on the graph path and on the persistent kernel (4 stages),
     // then the fused path and the other ring depths at the best shape
     for (const auto& sh : shapes)
-      for (int32_t path : {(int32_t)JACOBI_PATH_GRAPH, (int32_t)JACOBI_PATH_PERSISTENT})
-        if (!rc) rc = trial(path, kStreamStages, sh.first, sh.second);
+      for (int32_t path : {(int32_t)JACOBI_PATH_GRAPH, (int32_t)JACOBI_PATH_PERSISTENT, (int32_t)JACOBI_PATH_FUSED})
+        if (!rc && (only_path < 0 ? path != JACOBI_PATH_FUSED : path == only_path))
+          rc = trial(path, kStreamStages, sh.first, sh.second);
     const int64_t bz = r.zchunk;
     const int32_t bc = r.cw_cap;
-    if (!rc) rc = trial(JACOBI_PATH_FUSED, kStreamStages, bz, bc);
-    for (int32_t st = 3; st <= 6 && !rc; ++st) {
+    if (!rc && only_path < 0) rc = trial(JACOBI_PATH_FUSED, kStreamStages, bz, bc);
+    for (int32_t st = 3; st <= 6 && !rc && (only_path < 0 || only_path == JACOBI_PATH_PERSISTENT); ++st) {
       if (st == kStreamStages || t->plan.max_stage == 0) continue;  // no plane-streamed blocks: depth irrelevant
       Plan q = t->plan;
       plan_items(&q, bz, bc, 0, 1);
@@ -1405,6 +1407,19 @@ extern "C" int jacobi_autotune(jacobi_t* h, int64_t iters_per_trial, void* strea
   h->tables_dirty = true;
   if (out) *out = r;
   return JACOBI_OK;
+}
+
+extern "C" int jacobi_autotune(jacobi_t* h, int64_t iters_per_trial, void* stream, jacobi_tune_result* out) {
+  if (!h || iters_per_trial < 1) return set_error(JACOBI_EINVAL, "bad arguments to jacobi_autotune");
+  return autotune_search(h, iters_per_trial, stream, out, -1);
+}
+
+extern "C" int jacobi_autotune_path(jacobi_t* h, int32_t path, int64_t iters_per_trial, void* stream,
+                                    jacobi_tune_result* out) {
+  if (!h || iters_per_trial < 1 ||
+      (path != JACOBI_PATH_FUSED && path != JACOBI_PATH_GRAPH && path != JACOBI_PATH_PERSISTENT))
+    return set_error(JACOBI_EINVAL, "bad arguments to jacobi_autotune_path");
+  return autotune_search(h, iters_per_trial, stream, out, path);
 }
 
 int jacobi_block(const jacobi_t* h, int64_t block, jacobi_block_info* out) {

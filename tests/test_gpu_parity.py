@@ -581,6 +581,32 @@ def test_autotune_keeps_results(tmp_path, monkeypatch, oracle_mod):
         assert np.array_equal(tuned[g], J.interior_of(want))
 
 
+def test_autotune_path_keeps_path_and_results(tmp_path, monkeypatch, oracle_mod):
+    """The search restricted to the persistent path applies that path with its
+    best shape and ring depth, is cached apart from the full search, and the
+    tuned handle's iterates equal the oracle's; another path is refused."""
+    monkeypatch.setenv("JACOBI_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    grids, splits, inits, dtype, _ = _batched("jacobi3d-batched256-fp32")
+    grids, splits, inits = grids[:8], splits[:8], inits[:8]
+    with jg.Jacobi3D(grids, splits, dtype, inits) as s:
+        r = s.autotune(8, path="persistent")
+        assert r["path"] == "persistent" and r["n_tried"] >= 2 and not r["from_cache"]
+        info = s.info
+        assert jg.PATH_NAMES[info.path] == "persistent" and info.stages == r["stages"]
+        assert (info.zchunk, info.cw_cap) == (r["zchunk"], r["cw_cap"])
+        s.step(13)
+        s.sync()
+        tuned = [s.copy_out(g) for g in range(len(grids))]
+        with pytest.raises(jg.JacobiError):
+            jg.jacobi_autotune_path(s.h, "explicit", 8, s.stream)
+    with jg.Jacobi3D(grids, splits, dtype, inits) as s:
+        assert s.autotune(8, path="persistent")["from_cache"]
+        assert not s.autotune(8)["from_cache"]  # the full search has its own cache entry
+    for g in (0, 3, 7):
+        want = oracle_mod.jacobi(J.initial_grid(*grids[g], dtype=np.float32, **inits[g]), 13)
+        assert np.array_equal(tuned[g], J.interior_of(want))
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_shapes_give_identical_iterates(oracle_mod, dtype):
     """Every work-item shape (z-chunk depth, consumer-warp cap) on the graph

@@ -106,3 +106,11 @@ def test_workspace_rejects_oversized_blocks(lib):
         assert e.value.code == jg.JACOBI_EINVAL
     # the same extent split in two is fine
     jg.jacobi_workspace_bytes((4, 65528, 1), ("count", (1, 2, 1)), "f32")
+
+
+def test_autotune_path_rejects_bad_arguments(lib):
+    # validated before any device work: a null handle, a path the search does
+    # not cover, and a trial length below one iteration
+    for args in ((None, "persistent", 8), (None, "explicit", 8), (None, "graph", 0)):
+        with pytest.raises(jg.JacobiError):
+            jg.jacobi_autotune_path(*args)

@@ -1,6 +1,7 @@
 """Host-side pieces of bench.py (no GPU): the rule that ties committed ncu
 counters to the kernel sources they were taken from, the CPU baseline's
-sample, and the reference arm's JSON line at one rank."""
+sample, the reference arm's JSON line at one rank, the per-configuration
+paths and tuner calls, and the full-size solve's flag."""
 import json
 import os
 import subprocess
@@ -88,3 +89,67 @@ def test_instruction_roof_from_counters():
     assert min(roof, key=lambda k: roof[k]["bound_GLUPs"]) == "fp64"
     assert bench.instruction_roof(None, 1, 2000.0, 100) is None
     assert bench.instruction_roof(rec, 1, None, 100) is None
+
+
+def test_config_bench_paths_and_tuning(monkeypatch):
+    """config_bench maps its path names onto handles and tuner calls: "auto"
+    tunes everything from a graph-path handle, "persistent_tuned" tunes the
+    shape for a persistent-path handle; every step is timed by events on the
+    given stream (a fake library and fake events stand in for the GPU)."""
+    import types
+    import bench
+    import jacobi_inputs as J
+    made, tuned = [], []
+
+    class FakeHandle:
+        def __init__(self, grids, splits, dtype, inits, path="fused", stream=None):
+            made.append(path)
+            self.info = types.SimpleNamespace(zchunk=4, cw_cap=8, halo_bytes_per_iter=0)
+
+        def __enter__(self):
+            return self
+
+        def __exit__(self, *exc):
+            return False
+
+        def autotune(self, iters, path=None):
+            tuned.append((iters, path))
+            return {"path": path or "graph", "stages": 4}
+
+        def step(self, n):
+            pass
+
+        def kind_items(self):
+            return {"k": 1}
+
+    class FakeEvent:
+        def __init__(self, enable_timing=False):
+            pass
+
+        def record(self, stream=None):
+            pass
+
+        def synchronize(self):
+            pass
+
+        def elapsed_time(self, other):
+            return 2.0  # ms
+
+    jg = types.SimpleNamespace(Jacobi3D=FakeHandle)
+    torch = types.SimpleNamespace(cuda=types.SimpleNamespace(Event=FakeEvent))
+    out = bench.config_bench(jg, J, torch, "jacobi3d-fp64-64c-2x2x2", None, 3, iters=10,
+                             paths=("graph", "persistent_tuned", "auto"))
+    assert made == ["graph", "persistent", "graph"]
+    assert tuned == [(10, "persistent"), (10, None)]
+    assert "autotune" not in out["graph"] and out["persistent_tuned"]["autotune"]["path"] == "persistent"
+    # 64^3 points x 10 iterations per step, 2 ms per step
+    assert abs(out["graph"]["GLUPs"] - 64 ** 3 * 10 / 2e-3 / 1e9) < 1e-9
+    assert out["graph"]["us_per_iter"] == 2e3 / 10
+
+
+def test_solve_full_flag_is_parsed(monkeypatch):
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--solve-full"])
+    assert bench.parse_args().solve_full
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    assert not bench.parse_args().solve_full

@@ -829,7 +829,7 @@ def run_ours(args):
     if extras:
         configs = {}
         c1 = config_bench(jg, J, torch, "jacobi3d-fp64-64c-2x2x2", stream, 5,
-                          paths=("graph", "persistent", "fused", "auto"))
+                          paths=("graph", "persistent", "persistent_tuned", "fused", "auto"))
         c1["exchange_forms"] = exchange_forms(jg, J, torch, "jacobi3d-fp64-64c-2x2x2", 100, stream)
         configs["jacobi3d-fp64-64c-2x2x2"] = c1
         configs["jacobi3d-fp64-512c-8x8x8"] = {

@@ -277,6 +277,28 @@ def test_solve_matches_oracle(oracle_mod, path):
     assert np.array_equal(got, _mask_edges(want))
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_tile_only_persistent_solve_matches_oracle(oracle_mod, dtype):
+    """Persistent launches whose items are all tiles (the barrier-driven
+    kernel, the first iteration of a check launch fusing the residual):
+    iteration count, status and frozen state equal the oracle's solve, the
+    residual within the residual bar."""
+    grid = (37, 30, 26)
+    init = dict(bc="uniform", bc_seed=43, interior="zero")
+    npdt = np.float64 if dtype == "f64" else np.float32
+    u0 = J.initial_grid(*grid, dtype=npdt, **init)
+    tol, cap, check = 1e-6, 3000, 9
+    want, k, rel, st = oracle_mod.solve(u0, tol, cap, check)
+    with _solver(grid, ("shape", (16, 16, 16)), dtype, init, "persistent") as s:
+        s.set_shape(0, 0)  # every block as tiles
+        assert set(s.kind_items()) == {"tiles"}
+        it, grel, gst = s.solve(tol, cap, check)
+        got = s.copy_out(padded=True)
+    assert (it[0], gst[0]) == (k, st)
+    assert abs(grel[0] - rel) <= RES_TOL * rel
+    assert np.array_equal(got, _mask_edges(want))
+
+
 def test_solve_cap_and_stagnation(oracle_mod):
     grid = (16, 16, 16)
     init = dict(bc="linear_noise", bc_seed=3, noise_amp=1e-3, interior="zero")
